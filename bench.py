@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of the Splotch hot path on GB300 (one JSON line on stdout).
+
+A step is one full frame of the hot path (raster + tile count, scan, scatter,
+splat + final transform) over the resident synthetic particle set.  The default
+workload is the two-species 100 M-particle frame at 2048^2 with FP16 attribute
+storage and FP32 accumulation.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Under torchrun (N > 1) every rank renders its own replica of the frame (the
+path needs no collective for independent frames); the step time is the maximum
+over ranks and the value counts the particles of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mparticles/s and frames/s at 1 GB300; served p50/p99 latency; % HBM roofline"
+UNIT = "Mparticles/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def load_brightness():
+    p = os.path.join(ROOT, "tests", "golden", "brightness.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def make_workload(name: str):
+    """(particle set, camera, storage, description)."""
+    from paper_1606_04427_gb300 import synth
+    beta = load_brightness()
+    cache = os.environ.get("SPLOTCH_SYNTH_CACHE")
+    if name == "two_species_f16" or name == "two_species_f32":
+        ps = _cached(cache, "two_species", lambda: synth.two_species_set(70_000_000, 30_000_000, 2))
+        cam = synth.front_camera(2048, 2048)
+        storage = "f16" if name.endswith("f16") else "f32"
+        b = beta.get("two_species", [1.0, 1.0])
+    elif name == "clustered":
+        ps = _cached(cache, "clustered", lambda: synth.clustered_set(10_000_000, 1))
+        cam = synth.front_camera(1024, 1024)
+        storage = "f32"
+        b = beta.get("clustered", [1.0])
+    elif name == "plain":
+        ps = synth.plain_set(100_000, 0)
+        cam = synth.front_camera(256, 256)
+        storage = "f32"
+        b = beta.get("plain", [1.0])
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return ps.with_brightness(b), cam, storage
+
+
+def _cached(cache_dir, key, fn):
+    from paper_1606_04427_gb300 import synth
+    if not cache_dir:
+        return fn()
+    os.makedirs(cache_dir, exist_ok=True)
+    path = os.path.join(cache_dir, key + ".npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        nt = int(z["type_begin"].shape[0] - 1)
+        return synth.ParticleSet(z["x"], z["y"], z["z"], z["h"], z["intensity"], z["type_begin"],
+                                 [z[f"cmap{t}"] for t in range(nt)], z["brightness"], z["i_log"],
+                                 z["i_min"], z["i_max"], key)
+    ps = fn()
+    np.savez(path, x=ps.x, y=ps.y, z=ps.z, h=ps.h, intensity=ps.intensity, type_begin=ps.type_begin,
+             brightness=ps.brightness, i_log=ps.i_log, i_min=ps.i_min, i_max=ps.i_max,
+             **{f"cmap{t}": c for t, c in enumerate(ps.cmaps)})
+    return ps
+
+
+def attr_bytes(storage):
+    return 4 if storage == "f32" else 2
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(ps, cam, storage, budget_s=20.0):
+    """The FP64 oracle as it stands, on this host's cores, over a stride sample of the
+    frame's particles (full image), scaled to Mparticles/s."""
+    import oracle
+    n = ps.n
+    probe = max(1, n // 400)
+    idx = np.arange(0, n, probe)
+    t0 = time.perf_counter()
+    oracle.render(ps.subset(idx), cam, oracle.Params(), storage)
+    t_probe = time.perf_counter() - t0
+    frac = min(1.0, (budget_s / max(t_probe, 1e-3)) * (idx.shape[0] / n))
+    step = max(1, int(round(1.0 / frac)))
+    idx = np.arange(0, n, step)
+    t0 = time.perf_counter()
+    oracle.render(ps.subset(idx), cam, oracle.Params(), storage)
+    dt = time.perf_counter() - t0
+    return {"value": idx.shape[0] / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"every {step}th particle ({idx.shape[0]} of {n}), full {cam.width}x{cam.height} "
+                      f"frame, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    ps, cam, storage = make_workload(args.workload)
+    n = ps.n
+    step = max(1, n // args.ref_particles)
+    sub = ps.subset(np.arange(0, n, step))
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.render(sub, cam, oracle.Params(), storage)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    val = sub.n / (ms / 1e3) / 1e6
+    sample = f"every {step}th particle ({sub.n} of {n}) per step, full {cam.width}x{cam.height} frame"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args.workload, ps, cam, storage, None),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(name, ps, cam, storage, tile):
+    return {"workload": name, "n_particles": ps.n, "species": ps.n_types, "image": [cam.width, cam.height],
+            "storage": storage, "accumulation": "f32", "tile": tile,
+            "l2": f"inputs larger than L2: {ps.n * 5 * attr_bytes(storage) / 1e9:.2f} GB of attributes"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="two_species_f16")
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--ref-particles", type=int, default=2_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1606_04427_gb300 import build, render
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    build.build()
+
+    ps, cam, storage = make_workload(args.workload)
+    params = render.RenderParams(tile=args.tile)
+    stream = torch.cuda.current_stream()
+    scene = render.Scene(ps, storage)
+    out = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        scene.render([cam], params, out)
+    torch.cuda.synchronize()
+
+    # per-kernel durations (CUDA events on the launching stream, inside the library)
+    kt = {"count": [], "scan": [], "scatter": [], "splat": []}
+    sizes = None
+    for _ in range(max(3, min(args.steps, 10))):
+        scene.render([cam], render.RenderParams(tile=args.tile, timing=True), out)
+        t = render.last_timing()
+        for k in kt:
+            kt[k].append(t[k])
+        sizes = t
+    kms = {k: statistics.mean(v) for k, v in kt.items()}
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        scene.render([cam], params, out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # end to end through the public API: pinned host particles -> scene -> frame -> host image
+    h2d = ps.n * 5 * 4
+    d2h = cam.width * cam.height * 3 * 4
+    pinned = ps.with_brightness(ps.brightness)
+    for k in ("x", "y", "z", "h", "intensity"):
+        t = torch.from_numpy(getattr(ps, k)).pin_memory()
+        setattr(pinned, k, t.numpy())
+    host_img = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32).pin_memory()
+    e2e_times = []
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sc2 = render.Scene(pinned, storage)
+        sc2.render([cam], params, out)
+        host_img.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sc2.close()
+        if k > 0:
+            e2e_times.append(dt)
+    e2e_ms = 1e3 * statistics.mean(e2e_times)
+
+    if rank != 0:
+        return 0
+
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    b = attr_bytes(storage)
+    n = ps.n
+    P = sizes["pairs"]
+    WH = cam.width * cam.height
+    alg = {
+        "count": n * 4 * b,
+        "scan": 0,
+        "scatter": n * 5 * b + P * 16,
+        "splat": P * 16 + WH * 12,
+    }
+    dom = max(kms, key=lambda k: kms[k])
+    ach = alg[dom] / (kms[dom] * 1e-3) / 1e9
+    frame_alg = n * 5 * b + WH * 12
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": None, "peak_kind": f"{peak_kind} (copy bandwidth)",
+            "algorithmic_bytes_per_launch": alg[dom],
+            "frame_frac": frame_alg / (ms * 1e-3) / 1e9 / hbm}
+    value = world * n / (ms * 1e-3) / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(args.workload, ps, cam, storage, args.tile or None),
+            "frames_per_s": world * 1e3 / ms,
+            "kernels_ms": kms, "pairs": P, "work_items": sizes["items"], "split_tiles": sizes["splits"],
+            "roofline": roof,
+            "e2e": {"value": n / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 4 * args.steps, "clocks": clk}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(ps, cam, storage)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

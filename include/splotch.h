@@ -1,0 +1,247 @@
+/*
+ * splotch.h: C ABI of the GB300 (sm_103a) Splotch hot path.
+ *
+ * Method: Dykes, Gheller, Rivi, Krokos, "Splotch: porting and optimizing for the
+ * Xeon Phi".  A frame is: per-particle rasterisation (roto-translation and perspective
+ * projection with reference to a camera and look-at point, clipping, colour from a
+ * scalar through a runtime colormap; Section 2.1, Section 3.1), binning of particles
+ * into square image tiles with the rule "distance to tile centre < 0.75 radius +
+ * sqrt(2) tile / 2" (Section 3.2.1, tile-list pseudocode), and per-tile accumulation
+ * of each particle's Gaussian footprint, colour times scalar weight (Section 2.1,
+ * Section 3.2.2), followed by the per-pixel final transform.  The mode built here is
+ * absorption equal to emission, whose radiative-transfer update (Section 2.1) closes
+ * to O = 1 - exp(-a) with a the additive accumulation.
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *   camera: right-handed, vertical field of view, up vector projected out of the view
+ *     direction; pixel (i, j) has its centre at (i + 0.5, j + 0.5), row 0 at the top;
+ *   screen radius r = F h / z_c, support R = max(rfac r, r_min_px), Gaussian
+ *     sigma = sigma_over_R R truncated at distance < R (defaults 0.75, 0.75 px, 0.5);
+ *   colormap: linear interpolation between entries, emission = brightness x colour;
+ *   images: float32, row-major H x W x 3 (RGB interleaved).
+ *   Every decision that turns floating point into an integer (near-plane cull, pixel
+ *   coverage, tile membership) is evaluated in FP32 with each operation rounded once
+ *   to nearest-even and no fused multiply-add, in the order written in the comments
+ *   of splotch_render below; values (colours, weights, sums) are FP32.
+ *
+ * Errors: every call returns a status; nothing throws across the ABI.  On failure
+ * splotch_last_error() gives a one-line reason for the calling thread.
+ * Threading: a scene is read-only after creation and may be rendered concurrently
+ * from several host threads on different streams; each render call allocates its own
+ * workspace.  Calls on one plan must not overlap.
+ */
+#ifndef SPLOTCH_H
+#define SPLOTCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct splotch_scene splotch_scene; /* opaque, library-owned device-resident particles */
+typedef struct splotch_plan splotch_plan;   /* opaque, pre-sized multi-view render */
+
+typedef enum {
+    SPLOTCH_OK = 0,
+    SPLOTCH_ERR_INVALID_ARG = 1, /* rejected before any GPU work */
+    SPLOTCH_ERR_OOM = 2,         /* an allocation (callback or default) returned NULL */
+    SPLOTCH_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    SPLOTCH_ERR_CAPACITY = 4,    /* a plan's pre-sized buffers were too small for this frame */
+    SPLOTCH_ERR_TIMEOUT = 5,     /* a bounded device wait ran out (the kernel returned early) */
+    SPLOTCH_ERR_UNSUPPORTED = 6  /* valid request outside this build's limits (e.g. tile count) */
+} splotch_status;
+
+typedef enum { SPLOTCH_F32 = 0, SPLOTCH_F16 = 1, SPLOTCH_BF16 = 2 } splotch_storage;
+
+/* Device memory provider for scene storage and per-call workspaces.  alloc returns a
+ * device pointer aligned to at least 256 bytes (or NULL: the call fails with
+ * SPLOTCH_ERR_OOM); both callbacks are stream-ordered on `stream` (a cudaStream_t).
+ * All-NULL fields select the library's own stream-ordered memory pool. */
+typedef struct {
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, void *stream);
+    void *ctx;
+} splotch_allocator;
+
+/* Particle set (Section 2.1: positions, an intrinsic radius per particle, a scalar
+ * field mapped through a runtime colormap; Section 4.1: gas and star species).
+ * Species are contiguous index ranges [type_begin[t], type_begin[t+1]).
+ *   n            particle count, >= 0
+ *   n_types      1..255
+ *   type_begin   host, n_types + 1 entries, type_begin[0] = 0, non-decreasing, last = n
+ *   x y z h intensity   n floats each (FP32), on the device when on_device != 0, else host;
+ *                h > 0 (smoothing length, world units); all finite
+ *   storage      splotch_storage for the resident copy of x, y, z, h and the normalised
+ *                intensity (FP16 / BF16 round to nearest even from FP32)
+ *   cmap_rgb     host, per type a pointer to cmap_len[t] RGB triples (FP32), cmap_len >= 2
+ *   brightness   host, per type (emission = brightness x colour)
+ *   i_log        host, per type: 1 = take ln(max(I, 1e-30)) before ranging
+ *   i_min i_max  host, per type range of the (logged) intensity; NULL = the exact min / max
+ *                over the species (Section 2.1: ranging and normalisation).  The normalised
+ *                intensity clamp((I' - i_min) / (i_max - i_min), 0, 1), or 0 when
+ *                i_max <= i_min, selects the colour.
+ *   allocator    see splotch_allocator; stream: cudaStream_t used for the copies.
+ * Inputs may be freed once splotch_create_scene returns (it synchronises `stream`). */
+typedef struct {
+    int64_t n;
+    int32_t n_types;
+    const int64_t *type_begin;
+    const float *x, *y, *z, *h, *intensity;
+    int32_t on_device;
+    int32_t storage;
+    const float *const *cmap_rgb;
+    const int32_t *cmap_len;
+    const float *brightness;
+    const float *i_min;
+    const float *i_max;
+    const int32_t *i_log;
+    splotch_allocator allocator;
+    void *stream;
+} splotch_scene_desc;
+
+/* Camera (Section 2.1: supplied camera and look-at positions).  FP64 on the host; the
+ * library composes f = (L - E)/|L - E|, s = (f x U)/|f x U|, u = s x f, rows (s, u, f)
+ * with translations -(row . E), and F = (0.5 H) / tan(fov_deg pi / 360), then rounds
+ * each to FP32 (the only FP64 step).  Rejected: width or height < 1, fov outside
+ * (0, 180), z_near <= 0, eye == lookat, |f x U| <= 1e-9 |U|. */
+typedef struct {
+    double eye[3], lookat[3], up[3];
+    double fov_deg; /* vertical field of view, degrees */
+    double z_near;  /* particles with camera depth <= z_near are culled */
+    int32_t width, height;
+} splotch_camera;
+
+/* Render parameters.
+ *   tile          square tile edge in pixels, 1..64, with at most 16384 tiles per image;
+ *                 0 = 32 (or the smallest edge above 32 that meets the tile limit).
+ *                 Section 3.1: the tile size is a runtime parameter.
+ *   rfac          support radius factor, > 0 (0.75; Section 3.2.1 threshold)
+ *   sigma_over_R  Gaussian sigma as a fraction of the support, > 0 (0.5)
+ *   r_min_px      smallest support radius in pixels, >= 0 (0.75)
+ *   flags         SPLOTCH_OUT_ACCUM: write the accumulation a instead of 1 - exp(-a);
+ *                 SPLOTCH_SYNC: splotch_render waits for the frame and reports a device-side
+ *                 TIMEOUT before returning; SPLOTCH_PLAN_GRAPH: a plan captures its launch
+ *                 sequence into a CUDA graph on first launch and replays it afterwards;
+ *                 SPLOTCH_TIMING: splotch_render records CUDA events around each kernel on
+ *                 `stream`, waits for the frame and keeps the durations for
+ *                 splotch_last_timing. */
+typedef struct {
+    int32_t tile;
+    float rfac;
+    float sigma_over_R;
+    float r_min_px;
+    int32_t flags;
+} splotch_render_params;
+
+enum { SPLOTCH_OUT_ACCUM = 1, SPLOTCH_SYNC = 2, SPLOTCH_PLAN_GRAPH = 4, SPLOTCH_TIMING = 8 };
+
+/* Defaults listed above. */
+splotch_render_params splotch_default_params(void);
+
+/* Copy a particle set to the device (library-owned), normalise the intensity per species
+ * (Section 2.1 preprocessing) and store the attributes in the requested precision.
+ * Errors: INVALID_ARG (bad counts, ranges, pointers, colormaps, non-finite or h <= 0),
+ * OOM, CUDA.  *out is set only on success. */
+splotch_status splotch_create_scene(const splotch_scene_desc *desc, splotch_scene **out);
+
+/* Release a scene (NULL is accepted).  The caller guarantees no render on it is in flight. */
+splotch_status splotch_destroy(splotch_scene *scene);
+
+/* Scene facts: particle count, species count, storage, device bytes held. */
+splotch_status splotch_scene_info(const splotch_scene *scene, int64_t *n, int32_t *n_types,
+                                  int32_t *storage, int64_t *device_bytes);
+
+/* The FP32 camera parameters the kernels use: m = 3x4 row-major view matrix,
+ * p = {F, W/2, H/2, z_near}.  Host only. */
+splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], float p[4]);
+
+/* Render n_views >= 1 frames of one scene into out (device, n_views x H x W x 3 FP32; all
+ * cameras the same size).  Per view, per particle (FP32, each operation rounded once):
+ *   xc = ((m0 x + m1 y) + m2 z) + m3 (rows 1, 2 likewise), visible iff zc > z_near;
+ *   X = W/2 + (F xc)/zc, Y = H/2 - (F yc)/zc, r = (F h)/zc, R = max(rfac r, r_min_px);
+ *   pixel box i in [max(0, ceil(clamp((X - R) - 0.5, -2, W + 1)) - 1),
+ *                   min(W - 1, floor(clamp((X + R) - 0.5, -2, W + 1)) + 1)], rows likewise;
+ *   pixel (i, j) covered iff in the box and ((i + .5) - X)^2 + ((j + .5) - Y)^2 < R R;
+ *   tile (tx, ty) of edge T holds the particle iff it meets the box and
+ *     (cx - X)^2 + (cy - Y)^2 < (R + 0.70710677 T)^2, cx = (tx + .5) T, cy = (ty + .5) T;
+ *   a(i, j) = sum over covered particles of e exp(-d^2 / (sigma_over_R R)^2);
+ *   out = 1 - exp(-a) (or a with SPLOTCH_OUT_ACCUM).
+ * The call blocks until the particle-tile pair count of each view is known (to size the
+ * tile lists), then enqueues the rest on `stream` and returns; out is ready when `stream`
+ * reaches that point.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA, TIMEOUT. */
+splotch_status splotch_render(splotch_scene *scene, const splotch_camera *cams, int32_t n_views,
+                              const splotch_render_params *params, float *out, void *stream);
+
+/* Test hook: per-particle raster outputs for one view, out8 = device float[8][n]:
+ * X, Y, R, zc, e_r, e_g, e_b (emission = brightness x colour), active (0 / 1).
+ * Inactive particles have X = Y = R = 0 when culled by the near plane. */
+splotch_status splotch_debug_raster(splotch_scene *scene, const splotch_camera *cam,
+                                    const splotch_render_params *params, float *out8,
+                                    void *stream);
+
+/* Test hook: tile lists of one view.  counts: device int32[n_tiles]; offsets: device
+ * int64[n_tiles + 1]; members: device int32[capacity] particle indices, grouped by tile
+ * in tile order (row-major), order inside a tile unspecified; *total (host) = pair
+ * count.  Returns CAPACITY (with *total set) if capacity is too small.  Synchronous. */
+splotch_status splotch_debug_bins(splotch_scene *scene, const splotch_camera *cam,
+                                  const splotch_render_params *params, int32_t *counts,
+                                  int64_t *offsets, int32_t *members, int64_t capacity,
+                                  int64_t *total, void *stream);
+
+/* Batched multi-view plan: all views share W x H and tile size.  Creation renders the
+ * pair counts of `cams` once to size the tile lists (times `headroom` >= 1) and keeps
+ * every buffer; splotch_plan_launch then enqueues the whole frame batch (count, scan,
+ * scatter and one persistent splat launch over all views' work) with no host
+ * synchronisation, so it may be captured into a CUDA graph.  If a launch needs more
+ * pairs than were reserved, its kernels skip their work and splotch_plan_check reports
+ * SPLOTCH_ERR_CAPACITY with the pairs needed; recreate the plan then. */
+splotch_status splotch_plan_create(splotch_scene *scene, const splotch_camera *cams,
+                                   int32_t n_views, const splotch_render_params *params,
+                                   double headroom, void *stream, splotch_plan **out);
+
+/* Replace the plan's cameras (same count and image size); stream-ordered copy. */
+splotch_status splotch_plan_set_cameras(splotch_plan *plan, const splotch_camera *cams,
+                                        int32_t n_views, void *stream);
+
+/* Enqueue one batch render into out (device, n_views x H x W x 3 FP32). */
+splotch_status splotch_plan_launch(splotch_plan *plan, float *out, void *stream);
+
+/* Synchronise `stream` and report the last launch: OK, CAPACITY (pairs_needed set), or
+ * TIMEOUT.  pairs_needed may be NULL. */
+splotch_status splotch_plan_check(splotch_plan *plan, void *stream, int64_t *pairs_needed);
+
+/* Device bytes a plan holds (its workspace), and its tile size. */
+splotch_status splotch_plan_info(const splotch_plan *plan, int64_t *device_bytes,
+                                 int32_t *tile, int64_t *pair_capacity);
+
+/* Release a plan (NULL accepted). */
+splotch_status splotch_plan_destroy(splotch_plan *plan);
+
+/* Workspace bytes one splotch_render of `pairs` particle-tile pairs needs at this size,
+ * for admission control by HBM footprint. */
+int64_t splotch_workspace_bytes(const splotch_scene *scene, int32_t width, int32_t height,
+                                int32_t tile, int64_t pairs);
+
+/* Self-test of the bounded device wait every kernel uses: one CTA waits on a shared-memory
+ * mbarrier that nothing completes, gives up after ~limit_cycles SM cycles (1e3..1e10) and
+ * reports it.  Returns SPLOTCH_ERR_TIMEOUT when the wait ran out as designed, SPLOTCH_OK
+ * if the barrier completed (it cannot), INVALID_ARG / CUDA otherwise.  Synchronous. */
+splotch_status splotch_selftest_bounded_wait(int64_t limit_cycles, void *stream);
+
+/* Kernel durations (ms) of this thread's last splotch_render made with SPLOTCH_TIMING:
+ * ms[0] raster+count, ms[1] scan, ms[2] raster+scatter, ms[3] splat+final; and the
+ * frame's particle-tile pairs, work items and split tiles in counts[0..2].
+ * INVALID_ARG if no timed render has run on this thread. */
+splotch_status splotch_last_timing(double ms[4], int64_t counts[3]);
+
+/* Static strings. */
+const char *splotch_status_string(splotch_status status);
+const char *splotch_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPLOTCH_H */

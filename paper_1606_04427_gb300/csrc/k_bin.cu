@@ -1,0 +1,442 @@
+// Scene preparation and tile binning (count / scan / scatter) for the Splotch hot path.
+//
+// Section 3.1 builds, per tile, the list of particles that affect it; Section 3.2.1
+// gives the membership rule and notes that growing per-thread vectors stalled on
+// allocation.  Here the lists are one flat array sized exactly from a counting pass:
+//   k_count   streams the particles once (coalesced 16-byte SoA loads), rasterises
+//             them for a group of views, histograms tile memberships in shared memory
+//             and reserves each chunk's slice of every tile segment with one global
+//             atomic per (chunk, tile);
+//   k_scan    turns the counts into tile segment offsets and the splat's work items;
+//   k_scatter streams the particles again and writes a 16-byte record per
+//             (particle, tile) pair into its tile segment.
+#include "splotch_internal.cuh"
+
+namespace spl {
+
+// ---------------------------------------------------------------------------------------
+// Scene preparation (Section 2.1: ranging, normalisation, optional logarithm).
+
+__device__ __forceinline__ unsigned order_key(float f) {
+    unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__global__ void k_minmax(const float *__restrict__ I, int64_t begin, int64_t end, int i_log,
+                         unsigned *keys) {
+    unsigned lo = 0xFFFFFFFFu, hi = 0u;
+    for (int64_t i = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float v = I[i];
+        if (i_log) v = logf(fmaxf(v, 1e-30f));
+        if (!isfinite(v)) continue;
+        unsigned k = order_key(v);
+        lo = min(lo, k);
+        hi = max(hi, k);
+    }
+    for (int o = 16; o; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&keys[0], lo);
+        atomicMax(&keys[1], hi);
+    }
+}
+
+cudaError_t launch_minmax(int, const float *I, int64_t begin, int64_t end, int i_log, unsigned *keys,
+                          cudaStream_t st) {
+    if (end <= begin) return cudaSuccess;
+    int64_t blocks = (end - begin + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_minmax<<<(int)blocks, 256, 0, st>>>(I, begin, end, i_log, keys);
+    return cudaGetLastError();
+}
+
+template <typename T> __device__ __forceinline__ T to_store(float v);
+template <> __device__ __forceinline__ float to_store<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+template <typename T>
+__global__ void k_prepare(const float *__restrict__ x, const float *__restrict__ y,
+                          const float *__restrict__ z, const float *__restrict__ h,
+                          const float *__restrict__ I, int64_t n, int n_types,
+                          const int64_t *__restrict__ tb, const float *__restrict__ lo,
+                          const float *__restrict__ hi, const int *__restrict__ i_log, T *ox, T *oy,
+                          T *oz, T *oh, T *oit, int *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int a = 0, b = n_types - 1;  // species: last t with tb[t] <= i
+        while (a < b) {
+            int mid = (a + b + 1) >> 1;
+            if (tb[mid] <= i) a = mid; else b = mid - 1;
+        }
+        const float xv = x[i], yv = y[i], zv = z[i], hv = h[i], Iv = I[i];
+        if (!(isfinite(xv) && isfinite(yv) && isfinite(zv) && isfinite(hv) && hv > 0.0f && isfinite(Iv)))
+            atomicOr(bad, 1);
+        float v = i_log[a] ? logf(fmaxf(Iv, 1e-30f)) : Iv;
+        const float span = __fsub_rn(hi[a], lo[a]);
+        float t = span > 0.0f ? __fdiv_rn(__fsub_rn(v, lo[a]), span) : 0.0f;
+        t = fminf(fmaxf(t, 0.0f), 1.0f);
+        ox[i] = to_store<T>(xv);
+        oy[i] = to_store<T>(yv);
+        oz[i] = to_store<T>(zv);
+        oh[i] = to_store<T>(hv);
+        oit[i] = to_store<T>(t);
+    }
+}
+
+cudaError_t launch_prepare(const float *x, const float *y, const float *z, const float *h,
+                           const float *I, int64_t n, int n_types, const int64_t *type_begin,
+                           const float *lo, const float *hi, const int *i_log, int storage,
+                           void *ox, void *oy, void *oz, void *oh, void *oit, int *bad,
+                           cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    switch (storage) {
+    case 0:
+        k_prepare<float><<<(int)blocks, 256, 0, st>>>(x, y, z, h, I, n, n_types, type_begin, lo, hi, i_log,
+                                                      (float *)ox, (float *)oy, (float *)oz, (float *)oh,
+                                                      (float *)oit, bad);
+        break;
+    case 1:
+        k_prepare<__half><<<(int)blocks, 256, 0, st>>>(x, y, z, h, I, n, n_types, type_begin, lo, hi, i_log,
+                                                       (__half *)ox, (__half *)oy, (__half *)oz,
+                                                       (__half *)oh, (__half *)oit, bad);
+        break;
+    default:
+        k_prepare<__nv_bfloat16><<<(int)blocks, 256, 0, st>>>(
+            x, y, z, h, I, n, n_types, type_begin, lo, hi, i_log, (__nv_bfloat16 *)ox,
+            (__nv_bfloat16 *)oy, (__nv_bfloat16 *)oz, (__nv_bfloat16 *)oh, (__nv_bfloat16 *)oit, bad);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// k_count: raster a chunk of particles for up to G views and count tile memberships.
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_count(SceneDev sc, FrameDev fr) {
+    extern __shared__ int s_hist[];  // [g_n][n_tiles]
+    __shared__ ViewParams s_view[kMaxGroup];
+    const int b = blockIdx.x;
+    const int v0 = blockIdx.y * fr.G;
+    const int g_n = min(fr.G, fr.V - v0);
+    const int nt = fr.n_tiles;
+    for (int k = threadIdx.x; k < g_n * nt; k += blockDim.x) s_hist[k] = 0;
+    if (threadIdx.x < g_n) s_view[threadIdx.x] = fr.views[v0 + threadIdx.x];
+    __syncthreads();
+
+    constexpr int VEC = Store<S>::VEC;
+    const int64_t s = (int64_t)b * fr.chunk;
+    const int64_t e = min(sc.n, s + fr.chunk);
+    for (int64_t i = s + (int64_t)threadIdx.x * VEC; i < e; i += (int64_t)blockDim.x * VEC) {
+        float x[VEC], y[VEC], z[VEC], h[VEC];
+        Store<S>::load(sc.x, i, x);
+        Store<S>::load(sc.y, i, y);
+        Store<S>::load(sc.z, i, z);
+        Store<S>::load(sc.h, i, h);
+        for (int g = 0; g < g_n; ++g) {
+            const ViewParams &vp = s_view[g];
+            int *hist = s_hist + g * nt;
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                Raster r;
+                if (i + k < e && raster_one(vp, x[k], y[k], z[k], h[k], r)) {
+                    const int tx0 = r.i0 / vp.T, tx1 = r.i1 / vp.T;
+                    const int ty0 = r.j0 / vp.T, ty1 = r.j1 / vp.T;
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx)
+                            if (tile_member(vp, r.X, r.Y, r.R, tx, ty)) atomicAdd(&hist[ty * vp.ntx + tx], 1);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < g_n * nt; k += blockDim.x) {
+        const int c = s_hist[k];
+        if (c) {
+            const int g = k / nt, t = k - g * nt;
+            const int v = v0 + g;
+            const int base = atomicAdd(&fr.counts[v * nt + t], c);
+            fr.rel[((int64_t)v * fr.n_chunks + b) * nt + t] = base;
+        }
+    }
+}
+
+template <int S> static cudaError_t count_impl(const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
+    const size_t smem = (size_t)fr.G * fr.n_tiles * sizeof(int);
+    cudaError_t err = cudaFuncSetAttribute(k_count<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid(fr.n_chunks, (fr.V + fr.G - 1) / fr.G);
+    k_count<S><<<grid, kThreads, smem, st>>>(sc, fr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(int storage, const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
+    if (storage == 0) return count_impl<0>(sc, fr, st);
+    if (storage == 1) return count_impl<1>(sc, fr, st);
+    return count_impl<2>(sc, fr, st);
+}
+
+// ---------------------------------------------------------------------------------------
+// k_scan: one CTA.  Tile segment offsets (int64), work items (a tile with more than K
+// pairs is split into ceil(count / K) items) and scratch slots of split tiles.
+
+template <typename T> __device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive block scan (1024 threads); returns the exclusive prefix, *total = block sum.
+template <typename T> __device__ T block_excl_scan(T v, T *s_warp, T *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T incl = warp_incl_scan(v);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T w = s_warp[lane];
+        T wi = warp_incl_scan(w);
+        s_warp[lane] = wi - w;
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    T res = s_warp[warp] + incl - v;
+    *total = s_warp[32];
+    __syncthreads();
+    return res;
+}
+
+constexpr int kScanItems = 4;
+
+__global__ void __launch_bounds__(1024) k_scan(FrameDev fr, int target_items, int kmin) {
+    __shared__ long long s_l[33];
+    __shared__ int s_i[33];
+    __shared__ int s_j[33];
+    const int N = fr.V * fr.n_tiles;
+    // pass 1: total pairs and largest tile
+    long long sum = 0;
+    int mx = 0;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const int c = fr.counts[k];
+        sum += c;
+        mx = max(mx, c);
+    }
+    long long tot;
+    block_excl_scan<long long>(sum, s_l, &tot);
+    int mx_all;
+    {
+        for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) s_i[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int w = s_i[threadIdx.x];
+            for (int o = 16; o; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+            if (threadIdx.x == 0) s_i[32] = w;
+        }
+        __syncthreads();
+        mx_all = s_i[32];
+        __syncthreads();
+    }
+    long long K = (tot + target_items - 1) / (target_items > 0 ? target_items : 1);
+    if (K < kmin) K = kmin;
+    if (K > (1LL << 30)) K = (1LL << 30);
+
+    // pass 2: scans
+    long long run_p = 0;
+    int run_i = 0, run_s = 0;
+    for (int base = 0; base < N; base += blockDim.x * kScanItems) {
+        const int k0 = base + threadIdx.x * kScanItems;
+        int c[kScanItems], it[kScanItems], sp[kScanItems];
+        long long lp = 0;
+        int li = 0, ls = 0;
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            const int k = k0 + q;
+            c[q] = k < N ? fr.counts[k] : 0;
+            it[q] = k < N ? max(1, (int)((c[q] + K - 1) / K)) : 0;
+            sp[q] = (k < N && c[q] > K) ? 1 : 0;
+            lp += c[q];
+            li += it[q];
+            ls += sp[q];
+        }
+        long long tp;
+        int ti, ts;
+        long long ep = block_excl_scan<long long>(lp, s_l, &tp) + run_p;
+        int ei = block_excl_scan<int>(li, s_i, &ti) + run_i;
+        int es = block_excl_scan<int>(ls, s_j, &ts) + run_s;
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            const int k = k0 + q;
+            if (k < N) {
+                fr.offsets[k] = ep;
+                fr.item_off[k] = ei;
+                fr.split_slot[k] = sp[q] ? es : -1;
+            }
+            ep += c[q];
+            ei += it[q];
+            es += sp[q];
+        }
+        run_p += tp;
+        run_i += ti;
+        run_s += ts;
+    }
+    if (threadIdx.x == 0) {
+        fr.offsets[N] = run_p;
+        fr.item_off[N] = run_i;
+        fr.sizes[kSizePairs] = run_p;
+        fr.sizes[kSizeItems] = run_i;
+        fr.sizes[kSizeSplits] = run_s;
+        fr.sizes[kSizeK] = K;
+        fr.sizes[kSizeMaxCount] = mx_all;
+        const bool over = run_p > fr.pair_cap || run_i > fr.item_cap || run_s > fr.split_cap;
+        fr.status[kStatOverflow] = over ? 1 : 0;
+    }
+}
+
+cudaError_t launch_scan(const FrameDev &fr, int target_items, int kmin, cudaStream_t st) {
+    k_scan<<<1, 1024, 0, st>>>(fr, target_items, kmin);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// k_scatter: same chunks as k_count; every (particle, tile) pair becomes a record
+// {X, Y, R, type << 24 | 24-bit normalised intensity} in its tile segment.
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) {
+    if (fr.status[kStatOverflow]) return;
+    extern __shared__ int s_cur[];  // [g_n][n_tiles]
+    __shared__ ViewParams s_view[kMaxGroup];
+    __shared__ int64_t s_tb[kMaxTypes + 1];
+    const int b = blockIdx.x;
+    const int v0 = blockIdx.y * fr.G;
+    const int g_n = min(fr.G, fr.V - v0);
+    const int nt = fr.n_tiles;
+    for (int k = threadIdx.x; k < g_n * nt; k += blockDim.x) {
+        const int g = k / nt, t = k - g * nt;
+        s_cur[k] = fr.rel[((int64_t)(v0 + g) * fr.n_chunks + b) * nt + t];
+    }
+    if (threadIdx.x < g_n) s_view[threadIdx.x] = fr.views[v0 + threadIdx.x];
+    for (int k = threadIdx.x; k <= sc.n_types; k += blockDim.x) s_tb[k] = sc.type_begin[k];
+    __syncthreads();
+
+    constexpr int VEC = Store<S>::VEC;
+    const int64_t s = (int64_t)b * fr.chunk;
+    const int64_t e = min(sc.n, s + fr.chunk);
+    int type = 0;
+    for (int64_t i = s + (int64_t)threadIdx.x * VEC; i < e; i += (int64_t)blockDim.x * VEC) {
+        float x[VEC], y[VEC], z[VEC], h[VEC], it[VEC];
+        Store<S>::load(sc.x, i, x);
+        Store<S>::load(sc.y, i, y);
+        Store<S>::load(sc.z, i, z);
+        Store<S>::load(sc.h, i, h);
+        Store<S>::load(sc.it, i, it);
+        for (int g = 0; g < g_n; ++g) {
+            const ViewParams &vp = s_view[g];
+            int *cur = s_cur + g * nt;
+            const int64_t *seg = fr.offsets + (int64_t)(v0 + g) * nt;
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                Raster r;
+                if (i + k < e && raster_one(vp, x[k], y[k], z[k], h[k], r)) {
+                    while (type + 1 < sc.n_types && i + k >= s_tb[type + 1]) ++type;
+                    uint32_t q = __float2uint_rn(__fmul_rn(it[k], (float)kCodeMax));
+                    q = min(q, kCodeMax);
+                    const float4 rec = make_float4(r.X, r.Y, r.R, __uint_as_float(((uint32_t)type << 24) | q));
+                    const int tx0 = r.i0 / vp.T, tx1 = r.i1 / vp.T;
+                    const int ty0 = r.j0 / vp.T, ty1 = r.j1 / vp.T;
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx)
+                            if (tile_member(vp, r.X, r.Y, r.R, tx, ty)) {
+                                const int t = ty * vp.ntx + tx;
+                                const int loc = atomicAdd(&cur[t], 1);
+                                const int64_t pos = seg[t] + loc;
+                                fr.lists[pos] = rec;
+                                if (fr.pids) fr.pids[pos] = (int)(i + k);
+                            }
+                }
+            }
+        }
+    }
+}
+
+template <int S> static cudaError_t scatter_impl(const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
+    const size_t smem = (size_t)fr.G * fr.n_tiles * sizeof(int);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_scatter<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid(fr.n_chunks, (fr.V + fr.G - 1) / fr.G);
+    k_scatter<S><<<grid, kThreads, smem, st>>>(sc, fr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
+    if (storage == 0) return scatter_impl<0>(sc, fr, st);
+    if (storage == 1) return scatter_impl<1>(sc, fr, st);
+    return scatter_impl<2>(sc, fr, st);
+}
+
+// ---------------------------------------------------------------------------------------
+// Debug raster: X, Y, R, zc, colour (brightness x colormap of the stored normalised
+// intensity), active, for one view.
+
+template <int S>
+__global__ void k_debug_raster(SceneDev sc, const ViewParams *__restrict__ view, float *out8) {
+    const ViewParams vp = *view;
+    constexpr int VEC = Store<S>::VEC;
+    const int64_t n = sc.n;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * VEC; i < n;
+         i += (int64_t)gridDim.x * blockDim.x * VEC) {
+        float x[VEC], y[VEC], z[VEC], h[VEC], it[VEC];
+        Store<S>::load(sc.x, i, x);
+        Store<S>::load(sc.y, i, y);
+        Store<S>::load(sc.z, i, z);
+        Store<S>::load(sc.h, i, h);
+        Store<S>::load(sc.it, i, it);
+        for (int k = 0; k < VEC; ++k) {
+            const int64_t p = i + k;
+            if (p >= n) break;
+            Raster r;
+            r.X = r.Y = r.R = 0.0f;
+            const bool act = raster_one(vp, x[k], y[k], z[k], h[k], r);
+            int t = 0;
+            while (t + 1 < sc.n_types && p >= sc.type_begin[t + 1]) ++t;
+            const int len = sc.lut_len[t];
+            const float f = it[k] * (float)(len - 1);
+            const int kk = min((int)floorf(f), len - 2);
+            const float tau = f - (float)kk;
+            const float4 c0 = sc.lut[sc.lut_off[t] + kk], c1 = sc.lut[sc.lut_off[t] + kk + 1];
+            out8[0 * n + p] = r.X;
+            out8[1 * n + p] = r.Y;
+            out8[2 * n + p] = r.R;
+            out8[3 * n + p] = r.zc;
+            out8[4 * n + p] = (1.0f - tau) * c0.x + tau * c1.x;
+            out8[5 * n + p] = (1.0f - tau) * c0.y + tau * c1.y;
+            out8[6 * n + p] = (1.0f - tau) * c0.z + tau * c1.z;
+            out8[7 * n + p] = act ? 1.0f : 0.0f;
+        }
+    }
+}
+
+cudaError_t launch_debug_raster(int storage, const SceneDev &sc, const ViewParams *view, float *out8,
+                                cudaStream_t st) {
+    if (sc.n <= 0) return cudaSuccess;
+    int64_t blocks = (sc.n + 255 * 8) / (256 * 8) + 1;
+    if (blocks > 4096) blocks = 4096;
+    if (storage == 0) k_debug_raster<0><<<(int)blocks, 256, 0, st>>>(sc, view, out8);
+    else if (storage == 1) k_debug_raster<1><<<(int)blocks, 256, 0, st>>>(sc, view, out8);
+    else k_debug_raster<2><<<(int)blocks, 256, 0, st>>>(sc, view, out8);
+    return cudaGetLastError();
+}
+
+}  // namespace spl

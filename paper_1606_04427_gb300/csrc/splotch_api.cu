@@ -1,0 +1,1015 @@
+// Host runtime of the Splotch C ABI (include/splotch.h): scene residency, camera
+// composition, frame workspace sizing and the launch sequence count -> scan ->
+// scatter -> splat, the debug hooks and the pre-sized multi-view plan.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "splotch.h"
+#include "splotch_internal.cuh"
+
+using namespace spl;
+
+// -----------------------------------------------------------------------------------------
+// errors
+
+static thread_local std::string g_err;
+
+static splotch_status fail(splotch_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(SPLOTCH_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),      \
+                        __FILE__, __LINE__);                                                    \
+    } while (0)
+
+extern "C" const char *splotch_status_string(splotch_status s) {
+    switch (s) {
+    case SPLOTCH_OK: return "ok";
+    case SPLOTCH_ERR_INVALID_ARG: return "invalid argument";
+    case SPLOTCH_ERR_OOM: return "out of device memory";
+    case SPLOTCH_ERR_CUDA: return "CUDA error";
+    case SPLOTCH_ERR_CAPACITY: return "pre-sized capacity exceeded";
+    case SPLOTCH_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SPLOTCH_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *splotch_last_error(void) { return g_err.c_str(); }
+
+// -----------------------------------------------------------------------------------------
+// device memory: caller callbacks, or one stream-ordered pool per device
+
+static std::mutex g_pool_mu;
+static std::vector<cudaMemPool_t> g_pools;
+
+static cudaMemPool_t device_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pools[dev] = p;
+    }
+    return g_pools[dev];
+}
+
+struct Mem {
+    splotch_allocator a{};
+    int dev = 0;
+    bool custom() const { return a.alloc != nullptr; }
+    void *alloc(size_t bytes, cudaStream_t st) const {
+        if (bytes == 0) bytes = 256;
+        if (custom()) return a.alloc(a.ctx, bytes, (void *)st);
+        cudaMemPool_t pool = device_pool(dev);
+        if (!pool) return nullptr;
+        void *p = nullptr;
+        if (cudaMallocFromPoolAsync(&p, bytes, pool, st) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void release(void *p, cudaStream_t st) const {
+        if (!p) return;
+        if (custom()) {
+            if (a.free) a.free(a.ctx, p, (void *)st);
+        } else {
+            cudaFreeAsync(p, st);
+        }
+    }
+};
+
+static inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Sub-buffers carved from one allocation.
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    }
+};
+
+static int sm_count(int dev) {
+    static std::mutex mu;
+    static std::vector<int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+    if (!cache[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 1;
+    }
+    return cache[dev];
+}
+
+// small pinned host buffer per thread for size / status read-back
+struct HostBox {
+    int64_t *p = nullptr;
+    ~HostBox() {
+        if (p) cudaFreeHost(p);
+    }
+};
+static thread_local HostBox g_box;
+static int64_t *host_box() {
+    if (!g_box.p) {
+        if (cudaMallocHost((void **)&g_box.p, 64 * sizeof(int64_t)) != cudaSuccess) {
+            cudaGetLastError();
+            g_box.p = nullptr;
+        }
+    }
+    return g_box.p;
+}
+
+// per-thread kernel timing of the last SPLOTCH_TIMING render
+struct Timing {
+    cudaEvent_t ev[6] = {};
+    bool have = false;
+    double ms[4] = {0, 0, 0, 0};
+    int64_t counts[3] = {0, 0, 0};
+    ~Timing() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    bool init() {
+        for (auto &e : ev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+        return true;
+    }
+};
+static thread_local Timing g_timing;
+
+extern "C" splotch_status splotch_last_timing(double ms[4], int64_t counts[3]) {
+    if (!g_timing.have) return fail(SPLOTCH_ERR_INVALID_ARG, "no timed render on this thread");
+    if (ms)
+        for (int k = 0; k < 4; ++k) ms[k] = g_timing.ms[k];
+    if (counts)
+        for (int k = 0; k < 3; ++k) counts[k] = g_timing.counts[k];
+    return SPLOTCH_OK;
+}
+
+// -----------------------------------------------------------------------------------------
+// scene
+
+struct splotch_scene {
+    int dev = 0;
+    int64_t n = 0, n_pad = 0;
+    int n_types = 0;
+    int storage = 0;
+    std::vector<int64_t> type_begin;
+    Mem mem;
+    void *attr = nullptr;
+    void *meta = nullptr;
+    size_t attr_bytes = 0, meta_bytes = 0;
+    SceneDev dev_view{};
+};
+
+extern "C" splotch_render_params splotch_default_params(void) {
+    splotch_render_params p;
+    p.tile = 0;
+    p.rfac = 0.75f;
+    p.sigma_over_R = 0.5f;
+    p.r_min_px = 0.75f;
+    p.flags = 0;
+    return p;
+}
+
+static splotch_status validate_desc(const splotch_scene_desc *d) {
+    if (!d) return fail(SPLOTCH_ERR_INVALID_ARG, "desc is NULL");
+    if (d->n < 0) return fail(SPLOTCH_ERR_INVALID_ARG, "n < 0");
+    if (d->n >= (int64_t)1 << 31) return fail(SPLOTCH_ERR_UNSUPPORTED, "n >= 2^31 particles");
+    if (d->n_types < 1 || d->n_types > kMaxTypes)
+        return fail(SPLOTCH_ERR_INVALID_ARG, "n_types must be 1..%d", kMaxTypes);
+    if (!d->type_begin) return fail(SPLOTCH_ERR_INVALID_ARG, "type_begin is NULL");
+    if (d->type_begin[0] != 0 || d->type_begin[d->n_types] != d->n)
+        return fail(SPLOTCH_ERR_INVALID_ARG, "type_begin must start at 0 and end at n");
+    for (int t = 0; t < d->n_types; ++t)
+        if (d->type_begin[t + 1] < d->type_begin[t])
+            return fail(SPLOTCH_ERR_INVALID_ARG, "type_begin must be non-decreasing");
+    if (d->n > 0 && (!d->x || !d->y || !d->z || !d->h || !d->intensity))
+        return fail(SPLOTCH_ERR_INVALID_ARG, "particle array is NULL");
+    if (d->storage < 0 || d->storage > 2) return fail(SPLOTCH_ERR_INVALID_ARG, "bad storage");
+    if (!d->cmap_rgb || !d->cmap_len || !d->brightness || !d->i_log)
+        return fail(SPLOTCH_ERR_INVALID_ARG, "per-type array is NULL");
+    if ((d->i_min == nullptr) != (d->i_max == nullptr))
+        return fail(SPLOTCH_ERR_INVALID_ARG, "give both i_min and i_max or neither");
+    for (int t = 0; t < d->n_types; ++t) {
+        if (d->cmap_len[t] < 2 || d->cmap_len[t] > (1 << 20))
+            return fail(SPLOTCH_ERR_INVALID_ARG, "colormap %d needs 2..2^20 entries", t);
+        if (!d->cmap_rgb[t]) return fail(SPLOTCH_ERR_INVALID_ARG, "colormap %d is NULL", t);
+        for (int k = 0; k < 3 * d->cmap_len[t]; ++k)
+            if (!std::isfinite(d->cmap_rgb[t][k])) return fail(SPLOTCH_ERR_INVALID_ARG, "colormap %d not finite", t);
+        if (!std::isfinite(d->brightness[t])) return fail(SPLOTCH_ERR_INVALID_ARG, "brightness not finite");
+        if (d->i_min && !(std::isfinite(d->i_min[t]) && std::isfinite(d->i_max[t])))
+            return fail(SPLOTCH_ERR_INVALID_ARG, "intensity range not finite");
+    }
+    if ((d->allocator.alloc == nullptr) != (d->allocator.free == nullptr))
+        return fail(SPLOTCH_ERR_INVALID_ARG, "give both allocator callbacks or neither");
+    return SPLOTCH_OK;
+}
+
+static float order_key_inv(unsigned k) {
+    unsigned b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+
+extern "C" splotch_status splotch_create_scene(const splotch_scene_desc *d, splotch_scene **out) {
+    if (!out) return fail(SPLOTCH_ERR_INVALID_ARG, "out is NULL");
+    splotch_status s = validate_desc(d);
+    if (s != SPLOTCH_OK) return s;
+    cudaStream_t st = (cudaStream_t)d->stream;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+
+    splotch_scene *sc = new splotch_scene();
+    sc->dev = dev;
+    sc->n = d->n;
+    sc->n_pad = ((d->n + 7) / 8) * 8 + 8;
+    sc->n_types = d->n_types;
+    sc->storage = d->storage;
+    sc->type_begin.assign(d->type_begin, d->type_begin + d->n_types + 1);
+    sc->mem.a = d->allocator;
+    sc->mem.dev = dev;
+
+    auto cleanup = [&](splotch_status st_) {
+        if (sc->attr) sc->mem.release(sc->attr, st);
+        if (sc->meta) sc->mem.release(sc->meta, st);
+        cudaStreamSynchronize(st);
+        delete sc;
+        return st_;
+    };
+
+    const size_t elem = d->storage == 0 ? 4 : 2;
+    const size_t arr = align256((size_t)sc->n_pad * elem);
+    sc->attr_bytes = 5 * arr;
+    sc->attr = sc->mem.alloc(sc->attr_bytes, st);
+    if (!sc->attr) return cleanup(fail(SPLOTCH_ERR_OOM, "scene attributes (%zu bytes)", sc->attr_bytes));
+
+    // colormaps premultiplied by brightness, as float4
+    std::vector<int> lut_off(d->n_types), lut_len(d->n_types);
+    int total = 0;
+    for (int t = 0; t < d->n_types; ++t) {
+        lut_off[t] = total;
+        lut_len[t] = d->cmap_len[t];
+        total += d->cmap_len[t];
+    }
+    std::vector<float> lut(4 * (size_t)total);
+    for (int t = 0; t < d->n_types; ++t)
+        for (int k = 0; k < d->cmap_len[t]; ++k) {
+            for (int c = 0; c < 3; ++c)
+                lut[4 * (lut_off[t] + k) + c] = d->brightness[t] * d->cmap_rgb[t][3 * k + c];
+            lut[4 * (lut_off[t] + k) + 3] = 0.0f;
+        }
+    Carve cv;
+    const size_t o_tb = cv.take(sizeof(int64_t) * (d->n_types + 1));
+    const size_t o_lut = cv.take(sizeof(float) * lut.size());
+    const size_t o_off = cv.take(sizeof(int) * d->n_types);
+    const size_t o_len = cv.take(sizeof(int) * d->n_types);
+    sc->meta_bytes = cv.off;
+    sc->meta = sc->mem.alloc(sc->meta_bytes, st);
+    if (!sc->meta) return cleanup(fail(SPLOTCH_ERR_OOM, "scene metadata"));
+    char *mb = (char *)sc->meta;
+    cudaMemcpyAsync(mb + o_tb, d->type_begin, sizeof(int64_t) * (d->n_types + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(mb + o_lut, lut.data(), sizeof(float) * lut.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(mb + o_off, lut_off.data(), sizeof(int) * d->n_types, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(mb + o_len, lut_len.data(), sizeof(int) * d->n_types, cudaMemcpyHostToDevice, st);
+
+    char *ab = (char *)sc->attr;
+    if (cudaMemsetAsync(ab, 0, sc->attr_bytes, st) != cudaSuccess)
+        return cleanup(fail(SPLOTCH_ERR_CUDA, "memset scene"));
+
+    if (d->n > 0) {
+        // staging: FP32 inputs on the device, per-type range, validity flag
+        Carve sv;
+        const size_t f = sizeof(float) * (size_t)d->n;
+        const size_t o_in[5] = {sv.take(f), sv.take(f), sv.take(f), sv.take(f), sv.take(f)};
+        const size_t o_lo = sv.take(sizeof(float) * d->n_types);
+        const size_t o_hi = sv.take(sizeof(float) * d->n_types);
+        const size_t o_lg = sv.take(sizeof(int) * d->n_types);
+        const size_t o_keys = sv.take(sizeof(unsigned) * 2 * d->n_types);
+        const size_t o_bad = sv.take(sizeof(int));
+        const bool copy_in = !d->on_device;
+        char *stg = (char *)sc->mem.alloc(sv.off, st);
+        if (!stg) return cleanup(fail(SPLOTCH_ERR_OOM, "scene staging"));
+        const float *src[5] = {d->x, d->y, d->z, d->h, d->intensity};
+        const float *in[5];
+        for (int k = 0; k < 5; ++k) {
+            if (copy_in) {
+                cudaMemcpyAsync(stg + o_in[k], src[k], f, cudaMemcpyHostToDevice, st);
+                in[k] = (const float *)(stg + o_in[k]);
+            } else {
+                in[k] = src[k];
+            }
+        }
+        std::vector<int> lg(d->i_log, d->i_log + d->n_types);
+        cudaMemcpyAsync(stg + o_lg, lg.data(), sizeof(int) * d->n_types, cudaMemcpyHostToDevice, st);
+        std::vector<float> lo(d->n_types), hi(d->n_types);
+        if (d->i_min) {
+            for (int t = 0; t < d->n_types; ++t) {
+                lo[t] = d->i_min[t];
+                hi[t] = d->i_max[t];
+            }
+        } else {
+            std::vector<unsigned> keys(2 * d->n_types);
+            for (int t = 0; t < d->n_types; ++t) {
+                keys[2 * t] = 0xFFFFFFFFu;
+                keys[2 * t + 1] = 0u;
+            }
+            cudaMemcpyAsync(stg + o_keys, keys.data(), sizeof(unsigned) * keys.size(), cudaMemcpyHostToDevice, st);
+            for (int t = 0; t < d->n_types; ++t) {
+                cudaError_t e = launch_minmax(0, in[4], d->type_begin[t], d->type_begin[t + 1], d->i_log[t],
+                                              (unsigned *)(stg + o_keys) + 2 * t, st);
+                if (e != cudaSuccess) {
+                    sc->mem.release(stg, st);
+                    return cleanup(fail(SPLOTCH_ERR_CUDA, "minmax: %s", cudaGetErrorString(e)));
+                }
+            }
+            cudaMemcpyAsync(keys.data(), stg + o_keys, sizeof(unsigned) * keys.size(), cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            for (int t = 0; t < d->n_types; ++t) {
+                lo[t] = keys[2 * t] == 0xFFFFFFFFu ? 0.0f : order_key_inv(keys[2 * t]);
+                hi[t] = keys[2 * t + 1] == 0u ? 0.0f : order_key_inv(keys[2 * t + 1]);
+            }
+        }
+        cudaMemcpyAsync(stg + o_lo, lo.data(), sizeof(float) * d->n_types, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(stg + o_hi, hi.data(), sizeof(float) * d->n_types, cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(stg + o_bad, 0, sizeof(int), st);
+        cudaError_t e = launch_prepare(in[0], in[1], in[2], in[3], in[4], d->n, d->n_types,
+                                       (const int64_t *)(mb + o_tb), (const float *)(stg + o_lo),
+                                       (const float *)(stg + o_hi), (const int *)(stg + o_lg), d->storage,
+                                       ab, ab + arr, ab + 2 * arr, ab + 3 * arr, ab + 4 * arr,
+                                       (int *)(stg + o_bad), st);
+        int bad = 0;
+        cudaMemcpyAsync(&bad, stg + o_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaError_t se = cudaStreamSynchronize(st);
+        sc->mem.release(stg, st);
+        if (e != cudaSuccess || se != cudaSuccess)
+            return cleanup(fail(SPLOTCH_ERR_CUDA, "prepare: %s", cudaGetErrorString(e != cudaSuccess ? e : se)));
+        if (bad) return cleanup(fail(SPLOTCH_ERR_INVALID_ARG, "non-finite attribute or h <= 0"));
+    }
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (se != cudaSuccess) return cleanup(fail(SPLOTCH_ERR_CUDA, "create: %s", cudaGetErrorString(se)));
+
+    SceneDev &v = sc->dev_view;
+    v.x = ab;
+    v.y = ab + arr;
+    v.z = ab + 2 * arr;
+    v.h = ab + 3 * arr;
+    v.it = ab + 4 * arr;
+    v.n = sc->n;
+    v.n_types = sc->n_types;
+    v.type_begin = (const int64_t *)(mb + o_tb);
+    v.lut = (const float4 *)(mb + o_lut);
+    v.lut_off = (const int *)(mb + o_off);
+    v.lut_len = (const int *)(mb + o_len);
+    *out = sc;
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_destroy(splotch_scene *sc) {
+    if (!sc) return SPLOTCH_OK;
+    sc->mem.release(sc->attr, 0);
+    sc->mem.release(sc->meta, 0);
+    cudaStreamSynchronize(0);
+    delete sc;
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_scene_info(const splotch_scene *sc, int64_t *n, int32_t *n_types,
+                                             int32_t *storage, int64_t *device_bytes) {
+    if (!sc) return fail(SPLOTCH_ERR_INVALID_ARG, "scene is NULL");
+    if (n) *n = sc->n;
+    if (n_types) *n_types = sc->n_types;
+    if (storage) *storage = sc->storage;
+    if (device_bytes) *device_bytes = (int64_t)(sc->attr_bytes + sc->meta_bytes);
+    return SPLOTCH_OK;
+}
+
+// -----------------------------------------------------------------------------------------
+// camera (FP64, each operation rounded once, then each entry rounded to FP32)
+
+static double dot3(const double *a, const double *b) {
+    double t = a[0] * b[0];
+    t = t + a[1] * b[1];
+    t = t + a[2] * b[2];
+    return t;
+}
+static void cross3(const double *a, const double *b, double *o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static splotch_status compose_camera(const splotch_camera *c, float m[12], float p[4]) {
+    if (!c) return fail(SPLOTCH_ERR_INVALID_ARG, "camera is NULL");
+    if (c->width < 1 || c->height < 1) return fail(SPLOTCH_ERR_INVALID_ARG, "image size < 1");
+    if (!(c->fov_deg > 0.0 && c->fov_deg < 180.0)) return fail(SPLOTCH_ERR_INVALID_ARG, "fov outside (0, 180)");
+    if (!(c->z_near > 0.0)) return fail(SPLOTCH_ERR_INVALID_ARG, "z_near <= 0");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(c->eye[k]) || !std::isfinite(c->lookat[k]) || !std::isfinite(c->up[k]))
+            return fail(SPLOTCH_ERR_INVALID_ARG, "camera not finite");
+    const double d[3] = {c->lookat[0] - c->eye[0], c->lookat[1] - c->eye[1], c->lookat[2] - c->eye[2]};
+    const double nd = std::sqrt(dot3(d, d));
+    if (!(nd > 0.0)) return fail(SPLOTCH_ERR_INVALID_ARG, "eye == lookat");
+    const double f[3] = {d[0] / nd, d[1] / nd, d[2] / nd};
+    double s0[3];
+    cross3(f, c->up, s0);
+    const double ns = std::sqrt(dot3(s0, s0));
+    const double nu = std::sqrt(dot3(c->up, c->up));
+    if (!(ns > 1e-9 * nu)) return fail(SPLOTCH_ERR_INVALID_ARG, "up vector parallel to the view direction");
+    const double s[3] = {s0[0] / ns, s0[1] / ns, s0[2] / ns};
+    double u[3];
+    cross3(s, f, u);
+    const double *rows[3] = {s, u, f};
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) m[4 * r + k] = (float)rows[r][k];
+        m[4 * r + 3] = (float)(-dot3(rows[r], c->eye));
+    }
+    const double F = (0.5 * (double)c->height) / std::tan(c->fov_deg * (M_PI / 360.0));
+    p[0] = (float)F;
+    p[1] = 0.5f * (float)c->width;
+    p[2] = 0.5f * (float)c->height;
+    p[3] = (float)c->z_near;
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], float p[4]) {
+    if (!m || !p) return fail(SPLOTCH_ERR_INVALID_ARG, "output is NULL");
+    return compose_camera(cam, m, p);
+}
+
+static splotch_status check_params(const splotch_render_params *pr) {
+    if (!(pr->rfac > 0.0f) || !std::isfinite(pr->rfac)) return fail(SPLOTCH_ERR_INVALID_ARG, "rfac <= 0");
+    if (!(pr->sigma_over_R > 0.0f) || !std::isfinite(pr->sigma_over_R))
+        return fail(SPLOTCH_ERR_INVALID_ARG, "sigma_over_R <= 0");
+    if (!(pr->r_min_px >= 0.0f) || !std::isfinite(pr->r_min_px)) return fail(SPLOTCH_ERR_INVALID_ARG, "r_min_px < 0");
+    if (pr->tile < 0 || pr->tile > kMaxTile) return fail(SPLOTCH_ERR_INVALID_ARG, "tile outside 0..%d", kMaxTile);
+    return SPLOTCH_OK;
+}
+
+static int64_t n_tiles_for(int W, int H, int T) {
+    return (int64_t)((W + T - 1) / T) * ((H + T - 1) / T);
+}
+
+static splotch_status choose_tile(int W, int H, int requested, int *T) {
+    if (requested > 0) {
+        if (n_tiles_for(W, H, requested) > kMaxTiles)
+            return fail(SPLOTCH_ERR_UNSUPPORTED, "tile %d gives more than %d tiles for %dx%d", requested,
+                        kMaxTiles, W, H);
+        *T = requested;
+        return SPLOTCH_OK;
+    }
+    for (int t = 32; t <= kMaxTile; t += 8)
+        if (n_tiles_for(W, H, t) <= kMaxTiles) {
+            *T = t;
+            return SPLOTCH_OK;
+        }
+    return fail(SPLOTCH_ERR_UNSUPPORTED, "image %dx%d needs more than %d tiles of %d px", W, H, kMaxTiles, kMaxTile);
+}
+
+static splotch_status make_view(const splotch_camera *c, const splotch_render_params &pr, int T, ViewParams &v) {
+    float m[12], p[4];
+    splotch_status s = compose_camera(c, m, p);
+    if (s != SPLOTCH_OK) return s;
+    memcpy(v.m, m, sizeof(m));
+    v.F = p[0];
+    v.cx = p[1];
+    v.cy = p[2];
+    v.zn = p[3];
+    v.rfac = pr.rfac;
+    v.rmin = pr.r_min_px;
+    v.kexp = -kLog2e / (pr.sigma_over_R * pr.sigma_over_R);
+    v.hd = 0.70710677f * (float)T;
+    v.W = c->width;
+    v.H = c->height;
+    v.T = T;
+    v.ntx = (c->width + T - 1) / T;
+    v.nty = (c->height + T - 1) / T;
+    v.n_tiles = v.ntx * v.nty;
+    return SPLOTCH_OK;
+}
+
+// -----------------------------------------------------------------------------------------
+// frame workspace
+
+struct FrameHost {
+    int V = 0, G = 1, T = 32, n_tiles = 0, n_chunks = 1;
+    int64_t chunk = 0;
+    int storage = 0;
+    // fixed part
+    size_t o_views, o_counts, o_rel, o_offsets, o_item, o_split, o_sizes, o_status, o_queue, fixed_bytes;
+    // variable part (capacities)
+    int64_t pair_cap = 0;
+    int item_cap = 0, split_cap = 0;
+    bool pids = false;
+    size_t o_lists, o_pids, o_scratch, o_tickets, var_bytes;
+};
+
+static const int64_t kRelBudget = 256ll << 20;
+
+static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_tiles, int T) {
+    fh.V = V;
+    fh.T = T;
+    fh.n_tiles = n_tiles;
+    fh.storage = sc->storage;
+    fh.G = std::max(1, std::min({V, kMaxGroup, kMaxTiles / std::max(1, n_tiles)}));
+    const int n_sm = sm_count(sc->dev);
+    const int vec = sc->storage == 0 ? 4 : 8;
+    const int64_t unit = (int64_t)kThreads * vec;
+    const int64_t n_units = std::max<int64_t>(1, (sc->n + unit - 1) / unit);
+    const int groups = (V + fh.G - 1) / fh.G;
+    int64_t target = std::max<int64_t>(1, (4 * n_sm + groups - 1) / groups);
+    target = std::min(target, n_units);
+    const int64_t max_chunks = std::max<int64_t>(1, kRelBudget / (4ll * V * n_tiles));
+    int64_t nch = std::min(target, max_chunks);
+    const int64_t upc = (n_units + nch - 1) / nch;
+    fh.chunk = upc * unit;
+    fh.n_chunks = (int)std::max<int64_t>(1, (sc->n + fh.chunk - 1) / fh.chunk);
+    const int64_t N = (int64_t)V * n_tiles;
+    Carve cv;
+    fh.o_views = cv.take(sizeof(ViewParams) * V);
+    fh.o_counts = cv.take(sizeof(int) * N);
+    fh.o_rel = cv.take(sizeof(int) * N * fh.n_chunks);
+    fh.o_offsets = cv.take(sizeof(int64_t) * (N + 1));
+    fh.o_item = cv.take(sizeof(int) * (N + 1));
+    fh.o_split = cv.take(sizeof(int) * N);
+    fh.o_sizes = cv.take(sizeof(int64_t) * 8);
+    fh.o_status = cv.take(sizeof(int) * 4);
+    fh.o_queue = cv.take(sizeof(int) * 4);
+    fh.fixed_bytes = cv.off;
+}
+
+static void layout_var(FrameHost &fh, int64_t pairs, int items, int splits, bool pids) {
+    fh.pair_cap = pairs;
+    fh.item_cap = items;
+    fh.split_cap = splits;
+    fh.pids = pids;
+    Carve cv;
+    fh.o_lists = cv.take(sizeof(float4) * std::max<int64_t>(1, pairs));
+    fh.o_pids = pids ? cv.take(sizeof(int) * std::max<int64_t>(1, pairs)) : 0;
+    fh.o_scratch = cv.take(sizeof(float) * 3 * (size_t)fh.T * fh.T * std::max(1, splits));
+    fh.o_tickets = cv.take(sizeof(int) * std::max(1, splits));
+    fh.var_bytes = cv.off;
+}
+
+static FrameDev frame_dev(const FrameHost &fh, char *fixed, char *var) {
+    FrameDev fr{};
+    fr.views = (const ViewParams *)(fixed + fh.o_views);
+    fr.V = fh.V;
+    fr.G = fh.G;
+    fr.n_tiles = fh.n_tiles;
+    fr.T = fh.T;
+    fr.chunk = fh.chunk;
+    fr.n_chunks = fh.n_chunks;
+    fr.counts = (int *)(fixed + fh.o_counts);
+    fr.rel = (int *)(fixed + fh.o_rel);
+    fr.offsets = (int64_t *)(fixed + fh.o_offsets);
+    fr.item_off = (int *)(fixed + fh.o_item);
+    fr.split_slot = (int *)(fixed + fh.o_split);
+    fr.sizes = (int64_t *)(fixed + fh.o_sizes);
+    fr.status = (int *)(fixed + fh.o_status);
+    if (var) {
+        fr.lists = (float4 *)(var + fh.o_lists);
+        fr.pids = fh.pids ? (int *)(var + fh.o_pids) : nullptr;
+        fr.scratch = (float *)(var + fh.o_scratch);
+        fr.tickets = (int *)(var + fh.o_tickets);
+    }
+    fr.pair_cap = var ? fh.pair_cap : INT64_MAX;
+    fr.item_cap = var ? fh.item_cap : INT32_MAX;
+    fr.split_cap = var ? fh.split_cap : INT32_MAX;
+    return fr;
+}
+
+static int splat_grid(int dev, int T, int items) {
+    const int bps = std::max(1, splat_blocks_per_sm(T));
+    const int g = sm_count(dev) * bps;
+    return std::max(1, std::min(g, std::max(1, items)));
+}
+
+static int target_items(int dev, int T) { return sm_count(dev) * std::max(1, splat_blocks_per_sm(T)) * 4; }
+static const int kMinItemPairs = 2048;
+
+struct RenderSetup {
+    int W = 0, H = 0, T = 0, V = 0;
+    std::vector<ViewParams> views;
+    splotch_render_params pr{};
+};
+
+static splotch_status setup_views(const splotch_camera *cams, int n_views, const splotch_render_params *params,
+                                  RenderSetup &rs) {
+    if (!cams) return fail(SPLOTCH_ERR_INVALID_ARG, "cams is NULL");
+    if (n_views < 1) return fail(SPLOTCH_ERR_INVALID_ARG, "n_views < 1");
+    rs.pr = params ? *params : splotch_default_params();
+    splotch_status s = check_params(&rs.pr);
+    if (s != SPLOTCH_OK) return s;
+    rs.W = cams[0].width;
+    rs.H = cams[0].height;
+    for (int v = 0; v < n_views; ++v)
+        if (cams[v].width != rs.W || cams[v].height != rs.H)
+            return fail(SPLOTCH_ERR_INVALID_ARG, "all views must share the image size");
+    if (rs.W < 1 || rs.H < 1) return fail(SPLOTCH_ERR_INVALID_ARG, "image size < 1");
+    if ((int64_t)rs.W * rs.H > (int64_t)1 << 30) return fail(SPLOTCH_ERR_UNSUPPORTED, "image larger than 2^30 px");
+    s = choose_tile(rs.W, rs.H, rs.pr.tile, &rs.T);
+    if (s != SPLOTCH_OK) return s;
+    rs.V = n_views;
+    rs.views.resize(n_views);
+    for (int v = 0; v < n_views; ++v) {
+        s = make_view(&cams[v], rs.pr, rs.T, rs.views[v]);
+        if (s != SPLOTCH_OK) return s;
+    }
+    return SPLOTCH_OK;
+}
+
+// Count + scan for all views and read the sizes back (blocking).
+static splotch_status count_and_size(splotch_scene *sc, const RenderSetup &rs, FrameHost &fh, char *fixed,
+                                     cudaStream_t st, int64_t sizes[8], cudaEvent_t *ev = nullptr) {
+    FrameDev fr = frame_dev(fh, fixed, nullptr);
+    CUDA_TRY(cudaMemcpyAsync(fixed + fh.o_views, rs.views.data(), sizeof(ViewParams) * rs.V,
+                             cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(fixed + fh.o_counts, 0, sizeof(int) * (size_t)rs.V * fh.n_tiles, st));
+    CUDA_TRY(cudaMemsetAsync(fixed + fh.o_status, 0, sizeof(int) * 4, st));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[0], st));
+    CUDA_TRY(launch_count(sc->storage, sc->dev_view, fr, st));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
+    CUDA_TRY(launch_scan(fr, target_items(sc->dev, fh.T), kMinItemPairs, st));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
+    int64_t *box = host_box();
+    if (!box) return fail(SPLOTCH_ERR_OOM, "pinned host buffer");
+    CUDA_TRY(cudaMemcpyAsync(box, fixed + fh.o_sizes, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    memcpy(sizes, box, sizeof(int64_t) * 8);
+    return SPLOTCH_OK;
+}
+
+// Enqueue scatter + splat for a sized frame.
+static splotch_status scatter_and_splat(splotch_scene *sc, FrameHost &fh, char *fixed, char *var, float *out,
+                                        int out_accum, int items, cudaStream_t st, cudaEvent_t *ev = nullptr) {
+    FrameDev fr = frame_dev(fh, fixed, var);
+    CUDA_TRY(cudaMemsetAsync(fixed + fh.o_queue, 0, sizeof(int) * 4, st));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[3], st));
+    CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, st));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[4], st));
+    CUDA_TRY(launch_splat(sc->dev_view, fr, (int *)(fixed + fh.o_queue), out, out_accum,
+                          splat_grid(sc->dev, fh.T, items), st));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[5], st));
+    return SPLOTCH_OK;
+}
+
+
+static splotch_status render_frame(splotch_scene *sc, const RenderSetup &rs, float *out, cudaStream_t st,
+                                   bool sync, bool want_pids, int32_t *dbg_counts, int64_t *dbg_offsets,
+                                   int32_t *dbg_members, int64_t dbg_cap, int64_t *dbg_total) {
+    FrameHost fh;
+    layout_fixed(fh, sc, rs.V, rs.views[0].n_tiles, rs.T);
+    const bool timed = (rs.pr.flags & SPLOTCH_TIMING) != 0 && !dbg_members;
+    cudaEvent_t *ev = nullptr;
+    if (timed) {
+        if (!g_timing.init()) return fail(SPLOTCH_ERR_CUDA, "timing events");
+        ev = g_timing.ev;
+        g_timing.have = false;
+        sync = true;
+    }
+    char *fixed = (char *)sc->mem.alloc(fh.fixed_bytes, st);
+    if (!fixed) return fail(SPLOTCH_ERR_OOM, "frame workspace (%zu bytes)", fh.fixed_bytes);
+    int64_t sizes[8];
+    splotch_status s = count_and_size(sc, rs, fh, fixed, st, sizes, ev);
+    if (s != SPLOTCH_OK) {
+        sc->mem.release(fixed, st);
+        return s;
+    }
+    const int64_t P = sizes[kSizePairs];
+    const int items = (int)sizes[kSizeItems], splits = (int)sizes[kSizeSplits];
+    if (dbg_total) *dbg_total = P;
+    if (dbg_members && P > dbg_cap) {
+        sc->mem.release(fixed, st);
+        return fail(SPLOTCH_ERR_CAPACITY, "member capacity %lld < %lld pairs", (long long)dbg_cap, (long long)P);
+    }
+    layout_var(fh, P, items, splits, want_pids);
+    char *var = (char *)sc->mem.alloc(fh.var_bytes, st);
+    if (!var) {
+        sc->mem.release(fixed, st);
+        return fail(SPLOTCH_ERR_OOM, "tile lists (%zu bytes for %lld pairs)", fh.var_bytes, (long long)P);
+    }
+    s = SPLOTCH_OK;
+    do {
+        if (cudaMemsetAsync(var + fh.o_scratch, 0, fh.o_tickets - fh.o_scratch + sizeof(int) * std::max(1, splits),
+                            st) != cudaSuccess) {
+            s = fail(SPLOTCH_ERR_CUDA, "memset scratch");
+            break;
+        }
+        if (dbg_members) {
+            FrameDev fr = frame_dev(fh, fixed, var);
+            cudaError_t e = launch_scatter(sc->storage, sc->dev_view, fr, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(dbg_counts, fixed + fh.o_counts, sizeof(int) * fh.n_tiles, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(dbg_offsets, fixed + fh.o_offsets, sizeof(int64_t) * (fh.n_tiles + 1),
+                                    cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess && P > 0)
+                e = cudaMemcpyAsync(dbg_members, var + fh.o_pids, sizeof(int) * P, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = fail(SPLOTCH_ERR_CUDA, "debug bins: %s", cudaGetErrorString(e));
+            break;
+        }
+        s = scatter_and_splat(sc, fh, fixed, var, out, (rs.pr.flags & SPLOTCH_OUT_ACCUM) ? 1 : 0, items, st, ev);
+        if (s != SPLOTCH_OK) break;
+        if (sync) {
+            int64_t *box = host_box();
+            if (!box) {
+                s = fail(SPLOTCH_ERR_OOM, "pinned host buffer");
+                break;
+            }
+            cudaError_t e = cudaMemcpyAsync(box, fixed + fh.o_status, sizeof(int) * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                s = fail(SPLOTCH_ERR_CUDA, "render: %s", cudaGetErrorString(e));
+                break;
+            }
+            const int *stat = (const int *)box;
+            if (stat[kStatTimeout]) s = fail(SPLOTCH_ERR_TIMEOUT, "splat stage wait timed out");
+            if (timed && s == SPLOTCH_OK) {
+                float t[4] = {0, 0, 0, 0};
+                cudaEventElapsedTime(&t[0], ev[0], ev[1]);
+                cudaEventElapsedTime(&t[1], ev[1], ev[2]);
+                cudaEventElapsedTime(&t[2], ev[3], ev[4]);
+                cudaEventElapsedTime(&t[3], ev[4], ev[5]);
+                for (int k = 0; k < 4; ++k) g_timing.ms[k] = t[k];
+                g_timing.counts[0] = P;
+                g_timing.counts[1] = items;
+                g_timing.counts[2] = splits;
+                g_timing.have = true;
+            }
+        }
+    } while (0);
+    sc->mem.release(var, st);
+    sc->mem.release(fixed, st);
+    return s;
+}
+
+extern "C" splotch_status splotch_render(splotch_scene *sc, const splotch_camera *cams, int32_t n_views,
+                                         const splotch_render_params *params, float *out, void *stream) {
+    if (!sc) return fail(SPLOTCH_ERR_INVALID_ARG, "scene is NULL");
+    if (!out) return fail(SPLOTCH_ERR_INVALID_ARG, "out is NULL");
+    RenderSetup rs;
+    splotch_status s = setup_views(cams, n_views, params, rs);
+    if (s != SPLOTCH_OK) return s;
+    return render_frame(sc, rs, out, (cudaStream_t)stream, (rs.pr.flags & SPLOTCH_SYNC) != 0, false, nullptr,
+                        nullptr, nullptr, 0, nullptr);
+}
+
+extern "C" splotch_status splotch_debug_raster(splotch_scene *sc, const splotch_camera *cam,
+                                               const splotch_render_params *params, float *out8, void *stream) {
+    if (!sc || !out8) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    RenderSetup rs;
+    splotch_status s = setup_views(cam, 1, params, rs);
+    if (s != SPLOTCH_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *vp = sc->mem.alloc(sizeof(ViewParams), st);
+    if (!vp) return fail(SPLOTCH_ERR_OOM, "view params");
+    cudaError_t e = cudaMemcpyAsync(vp, rs.views.data(), sizeof(ViewParams), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_debug_raster(sc->storage, sc->dev_view, (const ViewParams *)vp, out8, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    sc->mem.release(vp, st);
+    if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "debug raster: %s", cudaGetErrorString(e));
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_debug_bins(splotch_scene *sc, const splotch_camera *cam,
+                                             const splotch_render_params *params, int32_t *counts, int64_t *offsets,
+                                             int32_t *members, int64_t capacity, int64_t *total, void *stream) {
+    if (!sc || !counts || !offsets || !members || !total) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    RenderSetup rs;
+    splotch_status s = setup_views(cam, 1, params, rs);
+    if (s != SPLOTCH_OK) return s;
+    return render_frame(sc, rs, nullptr, (cudaStream_t)stream, true, true, counts, offsets, members, capacity, total);
+}
+
+extern "C" int64_t splotch_workspace_bytes(const splotch_scene *sc, int32_t width, int32_t height, int32_t tile,
+                                           int64_t pairs) {
+    if (!sc || width < 1 || height < 1) return -1;
+    int T = 0;
+    if (choose_tile(width, height, tile, &T) != SPLOTCH_OK) return -1;
+    FrameHost fh;
+    layout_fixed(fh, sc, 1, (int)n_tiles_for(width, height, T), T);
+    const int64_t nt = n_tiles_for(width, height, T);
+    const int64_t splits = std::min<int64_t>(nt, pairs / kMinItemPairs + 1);
+    layout_var(fh, pairs, (int)(nt + pairs / kMinItemPairs + 1), (int)splits, false);
+    return (int64_t)(fh.fixed_bytes + fh.var_bytes);
+}
+
+// -----------------------------------------------------------------------------------------
+// plan: pre-sized multi-view frame, launchable without host synchronisation
+
+struct splotch_plan {
+    splotch_scene *sc = nullptr;
+    RenderSetup rs;
+    FrameHost fh;
+    char *fixed = nullptr, *var = nullptr;
+    int grid = 1;
+    int64_t *box = nullptr;  // pinned: sizes[8] then status[4] (as ints)
+    bool use_graph = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    float *exec_out = nullptr;
+};
+
+static splotch_status plan_enqueue(splotch_plan *pl, float *out, cudaStream_t st) {
+    splotch_scene *sc = pl->sc;
+    FrameHost &fh = pl->fh;
+    FrameDev fr = frame_dev(fh, pl->fixed, pl->var);
+    CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_counts, 0, sizeof(int) * (size_t)fh.V * fh.n_tiles, st));
+    CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_queue, 0, sizeof(int) * 4, st));
+    CUDA_TRY(launch_count(sc->storage, sc->dev_view, fr, st));
+    CUDA_TRY(launch_scan(fr, target_items(sc->dev, fh.T), kMinItemPairs, st));
+    CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, st));
+    CUDA_TRY(launch_splat(sc->dev_view, fr, (int *)(pl->fixed + fh.o_queue), out,
+                          (pl->rs.pr.flags & SPLOTCH_OUT_ACCUM) ? 1 : 0, pl->grid, st));
+    CUDA_TRY(cudaMemcpyAsync(pl->box, pl->fixed + fh.o_sizes, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(pl->box + 8, pl->fixed + fh.o_status, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_plan_destroy(splotch_plan *pl) {
+    if (!pl) return SPLOTCH_OK;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    cudaDeviceSynchronize();
+    if (pl->var) pl->sc->mem.release(pl->var, 0);
+    if (pl->fixed) pl->sc->mem.release(pl->fixed, 0);
+    if (pl->box) cudaFreeHost(pl->box);
+    cudaStreamSynchronize(0);
+    delete pl;
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_plan_create(splotch_scene *sc, const splotch_camera *cams, int32_t n_views,
+                                              const splotch_render_params *params, double headroom, void *stream,
+                                              splotch_plan **out) {
+    if (!sc || !out) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    if (!(headroom >= 1.0) || headroom > 100.0) return fail(SPLOTCH_ERR_INVALID_ARG, "headroom outside [1, 100]");
+    cudaStream_t st = (cudaStream_t)stream;
+    splotch_plan *pl = new splotch_plan();
+    pl->sc = sc;
+    splotch_status s = setup_views(cams, n_views, params, pl->rs);
+    if (s != SPLOTCH_OK) {
+        delete pl;
+        return s;
+    }
+    pl->use_graph = (pl->rs.pr.flags & SPLOTCH_PLAN_GRAPH) != 0;
+    layout_fixed(pl->fh, sc, pl->rs.V, pl->rs.views[0].n_tiles, pl->rs.T);
+    pl->fixed = (char *)sc->mem.alloc(pl->fh.fixed_bytes, st);
+    if (!pl->fixed) {
+        delete pl;
+        return fail(SPLOTCH_ERR_OOM, "plan workspace");
+    }
+    if (cudaMallocHost((void **)&pl->box, 16 * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        splotch_plan_destroy(pl);
+        return fail(SPLOTCH_ERR_OOM, "pinned host buffer");
+    }
+    int64_t sizes[8];
+    s = count_and_size(sc, pl->rs, pl->fh, pl->fixed, st, sizes);
+    if (s != SPLOTCH_OK) {
+        splotch_plan_destroy(pl);
+        return s;
+    }
+    const int64_t nt = (int64_t)pl->rs.V * pl->fh.n_tiles;
+    const int64_t pairs = (int64_t)std::ceil((double)sizes[kSizePairs] * headroom) + 1024;
+    const int64_t items = std::min<int64_t>(INT32_MAX / 2, (int64_t)std::ceil((double)sizes[kSizeItems] * headroom) + nt / 8 + 64);
+    const int64_t splits = std::min<int64_t>(nt, (int64_t)std::ceil((double)sizes[kSizeSplits] * headroom) + 64);
+    layout_var(pl->fh, pairs, (int)std::max<int64_t>(items, nt), (int)splits, false);
+    pl->var = (char *)sc->mem.alloc(pl->fh.var_bytes, st);
+    if (!pl->var) {
+        splotch_plan_destroy(pl);
+        return fail(SPLOTCH_ERR_OOM, "plan tile lists (%zu bytes)", pl->fh.var_bytes);
+    }
+    if (cudaMemsetAsync(pl->var + pl->fh.o_scratch, 0, pl->fh.var_bytes - pl->fh.o_scratch, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        splotch_plan_destroy(pl);
+        return fail(SPLOTCH_ERR_CUDA, "plan scratch");
+    }
+    pl->grid = splat_grid(sc->dev, pl->rs.T, INT32_MAX);
+    *out = pl;
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_plan_set_cameras(splotch_plan *pl, const splotch_camera *cams, int32_t n_views,
+                                                   void *stream) {
+    if (!pl) return fail(SPLOTCH_ERR_INVALID_ARG, "plan is NULL");
+    if (n_views != pl->rs.V) return fail(SPLOTCH_ERR_INVALID_ARG, "view count differs from the plan");
+    RenderSetup rs;
+    splotch_render_params pr = pl->rs.pr;
+    pr.tile = pl->rs.T;
+    splotch_status s = setup_views(cams, n_views, &pr, rs);
+    if (s != SPLOTCH_OK) return s;
+    if (rs.W != pl->rs.W || rs.H != pl->rs.H) return fail(SPLOTCH_ERR_INVALID_ARG, "image size differs from the plan");
+    pl->rs.views = rs.views;
+    CUDA_TRY(cudaMemcpyAsync(pl->fixed + pl->fh.o_views, pl->rs.views.data(), sizeof(ViewParams) * n_views,
+                             cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_plan_launch(splotch_plan *pl, float *out, void *stream) {
+    if (!pl || !out) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!pl->use_graph) return plan_enqueue(pl, out, st);
+    if (!pl->exec || pl->exec_out != out) {
+        if (pl->exec) {
+            cudaGraphExecDestroy(pl->exec);
+            pl->exec = nullptr;
+        }
+        if (!pl->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+        // one eager run sets kernel attributes outside capture
+        splotch_status s = plan_enqueue(pl, out, pl->cap_stream);
+        if (s != SPLOTCH_OK) return s;
+        CUDA_TRY(cudaStreamSynchronize(pl->cap_stream));
+        CUDA_TRY(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+        s = plan_enqueue(pl, out, pl->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+        if (s != SPLOTCH_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&pl->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        pl->exec_out = out;
+    }
+    CUDA_TRY(cudaGraphLaunch(pl->exec, st));
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_plan_check(splotch_plan *pl, void *stream, int64_t *pairs_needed) {
+    if (!pl) return fail(SPLOTCH_ERR_INVALID_ARG, "plan is NULL");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    const int64_t *sizes = pl->box;
+    const int *stat = (const int *)(pl->box + 8);
+    if (pairs_needed) *pairs_needed = sizes[kSizePairs];
+    if (stat[kStatTimeout]) return fail(SPLOTCH_ERR_TIMEOUT, "splat stage wait timed out");
+    if (stat[kStatOverflow])
+        return fail(SPLOTCH_ERR_CAPACITY, "frame needs %lld pairs / %lld items / %lld split tiles, plan holds %lld / %d / %d",
+                    (long long)sizes[kSizePairs], (long long)sizes[kSizeItems], (long long)sizes[kSizeSplits],
+                    (long long)pl->fh.pair_cap, pl->fh.item_cap, pl->fh.split_cap);
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_plan_info(const splotch_plan *pl, int64_t *device_bytes, int32_t *tile,
+                                            int64_t *pair_capacity) {
+    if (!pl) return fail(SPLOTCH_ERR_INVALID_ARG, "plan is NULL");
+    if (device_bytes) *device_bytes = (int64_t)(pl->fh.fixed_bytes + pl->fh.var_bytes);
+    if (tile) *tile = pl->rs.T;
+    if (pair_capacity) *pair_capacity = pl->fh.pair_cap;
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_selftest_bounded_wait(int64_t limit_cycles, void *stream) {
+    if (limit_cycles < 1000 || limit_cycles > 10000000000LL)
+        return fail(SPLOTCH_ERR_INVALID_ARG, "limit_cycles outside 1e3..1e10");
+    cudaStream_t st = (cudaStream_t)stream;
+    int *d = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&d, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(int), st));
+    cudaError_t e = launch_selftest_wait((long long)limit_cycles, d, st);
+    int r = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "selftest: %s", cudaGetErrorString(e));
+    if (r == 2) return fail(SPLOTCH_ERR_TIMEOUT, "bounded wait gave up after %lld cycles", (long long)limit_cycles);
+    if (r == 1) return SPLOTCH_OK;
+    return fail(SPLOTCH_ERR_CUDA, "selftest kernel did not report");
+}

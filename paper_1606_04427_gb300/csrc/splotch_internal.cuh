@@ -1,0 +1,260 @@
+// Internal declarations shared by the Splotch CUDA translation units (sm_103a).
+//
+// The per-particle raster rule lives here as device code: roto-translation and
+// perspective projection with the camera and look-at parameters, near-plane clipping,
+// screen radius from the smoothing length (Section 2.1), the pixel box, the tile rule
+// "distance to tile centre < 0.75 radius + sqrt(2) tile / 2" (Section 3.2.1) and the
+// per-pixel coverage of the Gaussian footprint.  Every comparison that decides an
+// integer is evaluated with explicitly rounded FP32 operations (no contraction) so the
+// decisions are reproducible from the ABI's written rule.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spl {
+
+constexpr int kMaxTiles = 16384;   // tiles per image (per-CTA shared histogram)
+constexpr int kMaxTile = 64;       // tile edge in pixels (shared accumulator)
+constexpr int kMaxTypes = 255;     // species (8-bit type field in the tile records)
+constexpr int kThreads = 256;      // CTA size of the particle-stream kernels
+constexpr int kSplatThreads = 256; // CTA size of the splat kernel
+constexpr int kSplatWarps = kSplatThreads / 32;
+constexpr int kStage = 512;        // tile records per bulk-copy stage
+constexpr int kMaxGroup = 16;      // views per CTA in the particle-stream kernels
+constexpr uint32_t kCodeMax = 16777215u;   // 24-bit normalised-intensity code
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Per-view constants, all FP32 except the integer geometry.
+struct ViewParams {
+    float m[12];          // 3x4 view matrix (rows s, u, f with translations)
+    float F, cx, cy, zn;  // focal length (px), image centre, near plane
+    float rfac, rmin;     // support factor and floor
+    float kexp;           // -log2(e) / sigma_over_R^2: w = exp2(d2 * kexp / R^2)
+    float hd;             // 0.70710677 * T, rounded once
+    int W, H, T, ntx, nty, n_tiles;
+};
+
+// Device-resident scene as the kernels see it.
+struct SceneDev {
+    const void *x, *y, *z, *h, *it;  // SoA in the storage type, padded
+    int64_t n;
+    int n_types;
+    const int64_t *type_begin;       // [n_types + 1]
+    const float4 *lut;               // brightness x colormap entries, all species
+    const int *lut_off;              // [n_types]
+    const int *lut_len;              // [n_types]
+};
+
+// Per-frame buffers (one frame = V views).
+struct FrameDev {
+    const ViewParams *views;  // [V]
+    int V, G;                 // views, views per particle-stream CTA
+    int n_tiles;              // per view
+    int T;                    // tile edge (all views)
+    int64_t chunk;            // particles per particle-stream CTA
+    int n_chunks;
+    int *counts;              // [V * n_tiles]
+    int *rel;                 // [V * n_chunks * n_tiles] chunk base inside the tile segment
+    int64_t *offsets;         // [V * n_tiles + 1] tile segment starts in `lists`
+    int *item_off;            // [V * n_tiles + 1] first work item of each tile
+    int *split_slot;          // [V * n_tiles] scratch slot of tiles split over items, else -1
+    int64_t *sizes;           // [8] pairs, items, splits, K, max tile count
+    int *status;              // [4] 0: capacity overflow, 1: timeout, 2: work queue
+    float4 *lists;            // [pair capacity] tile records (X, Y, R, code)
+    int *pids;                // [pair capacity] particle index per record, or null
+    float *scratch;           // [split capacity][3][T][T] partial accumulators
+    int *tickets;             // [split capacity]
+    int64_t pair_cap;
+    int item_cap, split_cap;
+};
+
+enum { kSizePairs = 0, kSizeItems = 1, kSizeSplits = 2, kSizeK = 3, kSizeMaxCount = 4 };
+enum { kStatOverflow = 0, kStatTimeout = 1, kStatQueue = 2 };
+
+// ------------------------------------------------------------------------------------
+// Storage loaders: VEC consecutive particles with one 16-byte load per attribute.
+
+template <int S> struct Store;
+template <> struct Store<0> {
+    static constexpr int VEC = 4;
+    static constexpr int BYTES = 4;
+    __device__ __forceinline__ static void load(const void *p, int64_t i, float *v) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(p) + i));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+};
+template <> struct Store<1> {
+    static constexpr int VEC = 8;
+    static constexpr int BYTES = 2;
+    __device__ __forceinline__ static void load(const void *p, int64_t i, float *v) {
+        uint4 a = __ldg(reinterpret_cast<const uint4 *>(static_cast<const __half *>(p) + i));
+        const __half2 *q = reinterpret_cast<const __half2 *>(&a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 f = __half22float2(q[k]);
+            v[2 * k] = f.x; v[2 * k + 1] = f.y;
+        }
+    }
+};
+template <> struct Store<2> {
+    static constexpr int VEC = 8;
+    static constexpr int BYTES = 2;
+    __device__ __forceinline__ static void load(const void *p, int64_t i, float *v) {
+        uint4 a = __ldg(reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(p) + i));
+        const __nv_bfloat162 *q = reinterpret_cast<const __nv_bfloat162 *>(&a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 f = __bfloat1622float2(q[k]);
+            v[2 * k] = f.x; v[2 * k + 1] = f.y;
+        }
+    }
+};
+
+// ------------------------------------------------------------------------------------
+// Raster rule (FP32, each operation rounded once, left to right).
+
+struct Raster {
+    float X, Y, R, zc;
+    int i0, i1, j0, j1;
+};
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Returns true when the particle is active: in front of the near plane, finite, and
+// with a non-empty pixel box inside the image.
+__device__ __forceinline__ bool raster_one(const ViewParams &v, float x, float y, float z, float h,
+                                           Raster &o) {
+    const float xc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(v.m[0], x), __fmul_rn(v.m[1], y)),
+                                         __fmul_rn(v.m[2], z)), v.m[3]);
+    const float yc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(v.m[4], x), __fmul_rn(v.m[5], y)),
+                                         __fmul_rn(v.m[6], z)), v.m[7]);
+    const float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(v.m[8], x), __fmul_rn(v.m[9], y)),
+                                         __fmul_rn(v.m[10], z)), v.m[11]);
+    o.zc = zc;
+    if (!(zc > v.zn)) return false;
+    const float X = __fadd_rn(v.cx, __fdiv_rn(__fmul_rn(v.F, xc), zc));
+    const float Y = __fsub_rn(v.cy, __fdiv_rn(__fmul_rn(v.F, yc), zc));
+    const float r = __fdiv_rn(__fmul_rn(v.F, h), zc);
+    float R = __fmul_rn(v.rfac, r);
+    if (!(R > v.rmin)) R = v.rmin;
+    o.X = X; o.Y = Y; o.R = R;
+    if (!(isfinite(X) && isfinite(Y) && isfinite(R))) return false;
+    const float wmax = (float)v.W + 1.0f, hmax = (float)v.H + 1.0f;
+    const float xl = clampf(__fsub_rn(__fsub_rn(X, R), 0.5f), -2.0f, wmax);
+    const float xh = clampf(__fsub_rn(__fadd_rn(X, R), 0.5f), -2.0f, wmax);
+    const float yl = clampf(__fsub_rn(__fsub_rn(Y, R), 0.5f), -2.0f, hmax);
+    const float yh = clampf(__fsub_rn(__fadd_rn(Y, R), 0.5f), -2.0f, hmax);
+    o.i0 = max(0, (int)ceilf(xl) - 1);
+    o.i1 = min(v.W - 1, (int)floorf(xh) + 1);
+    o.j0 = max(0, (int)ceilf(yl) - 1);
+    o.j1 = min(v.H - 1, (int)floorf(yh) + 1);
+    return o.i0 <= o.i1 && o.j0 <= o.j1;
+}
+
+// Box of a particle already rasterised (X, Y, R known): same expressions as above.
+__device__ __forceinline__ void pixel_box(const ViewParams &v, float X, float Y, float R, int &i0,
+                                          int &i1, int &j0, int &j1) {
+    const float wmax = (float)v.W + 1.0f, hmax = (float)v.H + 1.0f;
+    i0 = max(0, (int)ceilf(clampf(__fsub_rn(__fsub_rn(X, R), 0.5f), -2.0f, wmax)) - 1);
+    i1 = min(v.W - 1, (int)floorf(clampf(__fsub_rn(__fadd_rn(X, R), 0.5f), -2.0f, wmax)) + 1);
+    j0 = max(0, (int)ceilf(clampf(__fsub_rn(__fsub_rn(Y, R), 0.5f), -2.0f, hmax)) - 1);
+    j1 = min(v.H - 1, (int)floorf(clampf(__fsub_rn(__fadd_rn(Y, R), 0.5f), -2.0f, hmax)) + 1);
+}
+
+// Tile rule of Section 3.2.1 with the clamped support R standing for 0.75 radius.
+__device__ __forceinline__ bool tile_member(const ViewParams &v, float X, float Y, float R, int tx,
+                                            int ty) {
+    const float T = (float)v.T;
+    const float cx = __fmul_rn(__fadd_rn((float)tx, 0.5f), T);
+    const float cy = __fmul_rn(__fadd_rn((float)ty, 0.5f), T);
+    const float ex = __fsub_rn(cx, X), ey = __fsub_rn(cy, Y);
+    const float q = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
+    const float thr = __fadd_rn(R, v.hd);
+    return q < __fmul_rn(thr, thr);
+}
+
+// Inclusive warp scan of an int.
+__device__ __forceinline__ int warp_incl_scan_i(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------------------------
+// Bulk-copy (TMA, non-tensor) and mbarrier helpers.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~`limit` SM cycles and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// ------------------------------------------------------------------------------------
+// Host-side launchers (defined in the kernel translation units).
+
+cudaError_t launch_minmax(int storage_in_f32_only, const float *I, int64_t begin, int64_t end, int i_log,
+                          unsigned *keys, cudaStream_t st);
+cudaError_t launch_prepare(const float *x, const float *y, const float *z, const float *h,
+                           const float *I, int64_t n, int n_types, const int64_t *type_begin,
+                           const float *lo, const float *hi, const int *i_log, int storage,
+                           void *ox, void *oy, void *oz, void *oh, void *oit, int *bad,
+                           cudaStream_t st);
+cudaError_t launch_count(int storage, const SceneDev &sc, const FrameDev &fr, cudaStream_t st);
+cudaError_t launch_scan(const FrameDev &fr, int target_items, int kmin, cudaStream_t st);
+cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, cudaStream_t st);
+cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, float *out,
+                         int out_accum, int grid, cudaStream_t st);
+int splat_blocks_per_sm(int T);
+size_t splat_smem_bytes(int T);
+cudaError_t launch_selftest_wait(long long limit, int *result, cudaStream_t st);
+cudaError_t launch_debug_raster(int storage, const SceneDev &sc, const ViewParams *view,
+                                float *out8, cudaStream_t st);
+
+}  // namespace spl
