@@ -1,0 +1,216 @@
+"""Continuous-batching render server over particle sets resident on the GPU.
+
+Requests (set, camera) arrive at any time.  A request is admitted when a slot (a
+worker thread with its own CUDA stream) is free and its estimated device footprint
+(frame workspace + tile lists + image) fits in the remaining HBM budget; admitted
+requests render concurrently on their streams, so a request that arrives while
+others are on the GPU starts as soon as a slot and memory free up.  Latency is
+arrival to completion; the server reports throughput and p50 / p99.
+
+The paper's analogue is several MPI tasks sharing one coprocessor to keep it busy
+(Section 3.2.1, Section 4.2.1); here the tasks are streams of one process.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import render
+
+
+@dataclass
+class Completed:
+    request_id: int
+    set_index: int
+    width: int
+    height: int
+    arrival: float
+    start: float
+    finish: float
+    pairs: int
+    reserved_bytes: int
+    image: Optional[torch.Tensor] = None
+
+    @property
+    def latency(self) -> float:
+        return self.finish - self.arrival
+
+
+@dataclass
+class _Pending:
+    request_id: int
+    set_index: int
+    camera: object
+    arrival: float
+    estimate: int = 0
+    bypassed: int = 0
+
+
+class Server:
+    """``scenes``: resident :class:`render.Scene` objects.  ``slots``: concurrent
+    requests (one CUDA stream each).  ``hbm_budget``: bytes the in-flight requests may
+    reserve (default 80 % of the free device memory at construction)."""
+
+    def __init__(self, scenes: Sequence[render.Scene], slots: int = 4, hbm_budget: Optional[int] = None,
+                 params: Optional[render.RenderParams] = None, keep_images: bool = False,
+                 max_bypass: int = 8):
+        self.scenes = list(scenes)
+        self.slots = slots
+        if hbm_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            hbm_budget = int(0.8 * free)
+        self.budget = int(hbm_budget)
+        base = params or render.RenderParams()
+        self.params = render.RenderParams(**{**base.__dict__, "timing": True})
+        self.keep_images = keep_images
+        self.max_bypass = max_bypass
+        self.reserved = 0
+        self.peak_reserved = 0
+        self.ratio: Dict[tuple, float] = {}
+        self.cv = threading.Condition()
+        self.queue: deque = deque()
+        self.done: List[Completed] = []
+        self.errors: List[str] = []
+        self.in_flight = 0
+        self.next_id = 0
+        self.stop = False
+        self.t0 = time.perf_counter()
+        self.device = torch.cuda.current_device()
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.threads = [threading.Thread(target=self._worker, args=(k,), daemon=True) for k in range(slots)]
+        for t in self.threads:
+            t.start()
+
+    # ---------------------------------------------------------------------------------
+    def _key(self, set_index, cam):
+        return (set_index, int(cam.width), int(cam.height))
+
+    def estimate(self, set_index: int, cam) -> int:
+        """Device bytes a request is expected to need: the library's workspace for the
+        predicted pair count (largest pairs / particle seen for this set and size,
+        2.0 before any) plus the output image."""
+        sc = self.scenes[set_index]
+        ratio = self.ratio.get(self._key(set_index, cam), 2.0)
+        pairs = int(ratio * max(1, sc.n)) + 1024
+        ws = sc.workspace_bytes(cam.width, cam.height, self.params.tile, pairs)
+        return int(ws) + int(cam.width) * int(cam.height) * 12
+
+    def submit(self, set_index: int, cam, arrival: Optional[float] = None) -> int:
+        with self.cv:
+            rid = self.next_id
+            self.next_id += 1
+            p = _Pending(rid, set_index, cam, self.now() if arrival is None else arrival)
+            p.estimate = self.estimate(set_index, cam)
+            self.queue.append(p)
+            self.cv.notify_all()
+            return rid
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def _pick(self) -> Optional[_Pending]:
+        """Earliest queued request that fits the free budget; a request passed over
+        `max_bypass` times blocks later ones until it fits.  With nothing in flight
+        the head is admitted whatever its estimate (so no request waits forever)."""
+        free = self.budget - self.reserved
+        for k, p in enumerate(self.queue):
+            if p.estimate <= free or self.in_flight == 0:
+                for q in list(self.queue)[:k]:
+                    q.bypassed += 1
+                del self.queue[k]
+                return p
+            if p.bypassed >= self.max_bypass:
+                return None
+        return None
+
+    def _worker(self, k: int):
+        torch.cuda.set_device(self.device)
+        stream = self.streams[k]
+        while True:
+            with self.cv:
+                p = None
+                while not self.stop:
+                    p = self._pick()
+                    if p is not None:
+                        break
+                    self.cv.wait(timeout=0.05)
+                if p is None:
+                    return
+                self.reserved += p.estimate
+                self.peak_reserved = max(self.peak_reserved, self.reserved)
+                self.in_flight += 1
+            start = self.now()
+            pairs = 0
+            img = None
+            try:
+                cam = p.camera
+                with torch.cuda.stream(stream):
+                    img = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+                self.scenes[p.set_index].render([cam], self.params, img, stream=stream)
+                pairs = render.last_timing()["pairs"]
+            except Exception as e:  # a failed request is reported, the server keeps going
+                with self.cv:
+                    self.errors.append(f"request {p.request_id}: {e}")
+            finish = self.now()
+            with self.cv:
+                self.reserved -= p.estimate
+                self.in_flight -= 1
+                key = self._key(p.set_index, p.camera)
+                n = max(1, self.scenes[p.set_index].n)
+                self.ratio[key] = max(self.ratio.get(key, 0.0), pairs / n)
+                self.done.append(Completed(p.request_id, p.set_index, int(p.camera.width),
+                                           int(p.camera.height), p.arrival, start, finish, pairs,
+                                           p.estimate, img[0] if (self.keep_images and img is not None) else None))
+                self.cv.notify_all()
+
+    def wait_all(self, timeout: Optional[float] = None) -> None:
+        t_end = None if timeout is None else time.perf_counter() + timeout
+        with self.cv:
+            while self.queue or self.in_flight:
+                left = None if t_end is None else t_end - time.perf_counter()
+                if left is not None and left <= 0:
+                    raise TimeoutError("server did not drain")
+                self.cv.wait(timeout=0.05 if left is None else min(0.05, left))
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify_all()
+        for t in self.threads:
+            t.join(timeout=10)
+
+    # ---------------------------------------------------------------------------------
+    def run_trace(self, requests: Sequence, time_scale: float = 1.0) -> dict:
+        """Replay requests (objects with set_index, camera, arrival_s) in real time,
+        wait for all and return the statistics of this trace."""
+        first = len(self.done)
+        t_base = self.now()
+        for r in requests:
+            t_arr = t_base + r.arrival_s * time_scale
+            dt = t_arr - self.now()
+            if dt > 0:
+                time.sleep(dt)
+            self.submit(r.set_index, r.camera, arrival=t_arr)
+        self.wait_all()
+        return stats(self.done[first:], [self.scenes[i].n for i in range(len(self.scenes))])
+
+
+def stats(done: Sequence[Completed], set_sizes: Sequence[int]) -> dict:
+    if not done:
+        return {"requests": 0}
+    lat = np.array([d.latency for d in done])
+    t0 = min(d.arrival for d in done)
+    t1 = max(d.finish for d in done)
+    parts = sum(set_sizes[d.set_index] for d in done)
+    span = max(t1 - t0, 1e-9)
+    return {"requests": len(done), "seconds": span, "requests_per_s": len(done) / span,
+            "mparticles_per_s": parts / span / 1e6, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_ms": 1e3 * float(lat.mean()),
+            "max_ms": 1e3 * float(lat.max()),
+            "pairs_per_request": float(np.mean([d.pairs for d in done]))}
