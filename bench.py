@@ -50,6 +50,11 @@ def make_workload(name: str):
         cam = synth.front_camera(2048, 2048)
         storage = "f16" if name.endswith("f16") else "f32"
         b = beta.get("two_species", [1.0, 1.0])
+    elif name == "two_species_small":
+        ps = _cached(cache, "two_species_small", lambda: synth.two_species_set(7_000_000, 3_000_000, 2))
+        cam = synth.front_camera(2048, 2048)
+        storage = "f16"
+        b = [v * 10 for v in beta.get("two_species", [0.1, 0.1])]
     elif name == "clustered":
         ps = _cached(cache, "clustered", lambda: synth.clustered_set(10_000_000, 1))
         cam = synth.front_camera(1024, 1024)
@@ -198,6 +203,19 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(value: float) -> float:
+    """The largest value over all ranks (the step time of the slowest GPU); a no-op
+    outside torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def config_dict(name, ps, cam, storage, tile):
     return {"workload": name, "n_particles": ps.n, "species": ps.n_types, "image": [cam.width, cam.height],
             "storage": storage, "accumulation": "f32", "tile": tile,
@@ -273,32 +291,31 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms)
 
     # end to end through the public API: pinned host particles -> scene -> frame -> host image
     h2d = ps.n * 5 * 4
     d2h = cam.width * cam.height * 3 * 4
-    pinned = ps.with_brightness(ps.brightness)
-    for k in ("x", "y", "z", "h", "intensity"):
-        t = torch.from_numpy(getattr(ps, k)).pin_memory()
-        setattr(pinned, k, t.numpy())
-    host_img = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32).pin_memory()
-    e2e_times = []
-    for k in range(args.e2e_steps + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sc2 = render.Scene(pinned, storage)
-        sc2.render([cam], params, out)
-        host_img.copy_(out, non_blocking=True)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        sc2.close()
-        if k > 0:
-            e2e_times.append(dt)
-    e2e_ms = 1e3 * statistics.mean(e2e_times)
+    e2e_ms = None
+    if args.e2e_steps > 0:
+        pinned = ps.with_brightness(ps.brightness)
+        for k in ("x", "y", "z", "h", "intensity"):
+            t = torch.from_numpy(getattr(ps, k)).pin_memory()
+            setattr(pinned, k, t.numpy())
+        host_img = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32).pin_memory()
+        e2e_times = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sc2 = render.Scene(pinned, storage)
+            sc2.render([cam], params, out)
+            host_img.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            sc2.close()
+            if k > 0:
+                e2e_times.append(dt)
+        e2e_ms = 1e3 * statistics.mean(e2e_times)
 
     if rank != 0:
         return 0
@@ -330,8 +347,9 @@ def main():
             "frames_per_s": world * 1e3 / ms,
             "kernels_ms": kms, "pairs": P, "work_items": sizes["items"], "split_tiles": sizes["splits"],
             "roofline": roof,
-            "e2e": {"value": n / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": None if e2e_ms is None else {
+                "value": n / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 4 * args.steps, "clocks": clk}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ps, cam, storage)

@@ -120,6 +120,9 @@ typedef struct {
  *   rfac          support radius factor, > 0 (0.75; Section 3.2.1 threshold)
  *   sigma_over_R  Gaussian sigma as a fraction of the support, > 0 (0.5)
  *   r_min_px      smallest support radius in pixels, >= 0 (0.75)
+ *   block_particles  particles each CTA of the raster / count / scatter kernels streams,
+ *                 rounded up to a multiple of 1024 (FP32) or 2048 (FP16 / BF16);
+ *                 0 = about four CTAs per SM.  A tuning knob with no effect on results.
  *   flags         SPLOTCH_OUT_ACCUM: write the accumulation a instead of 1 - exp(-a);
  *                 SPLOTCH_SYNC: splotch_render waits for the frame and reports a device-side
  *                 TIMEOUT before returning; SPLOTCH_PLAN_GRAPH: a plan captures its launch
@@ -132,6 +135,7 @@ typedef struct {
     float rfac;
     float sigma_over_R;
     float r_min_px;
+    int32_t block_particles;
     int32_t flags;
 } splotch_render_params;
 
@@ -173,6 +177,12 @@ splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], flo
  * reaches that point.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA, TIMEOUT. */
 splotch_status splotch_render(splotch_scene *scene, const splotch_camera *cams, int32_t n_views,
                               const splotch_render_params *params, float *out, void *stream);
+
+/* Final transform in place: a[k] <- 1 - exp(-a[k]) for k < count (device FP32 buffer).
+ * With SPLOTCH_OUT_ACCUM renders this finishes an accumulation image, e.g. after the
+ * accumulations of several particle shards have been summed (the mode is additive,
+ * Section 2.1 and Section 3.2.2).  Asynchronous on `stream`; INVALID_ARG for count < 0. */
+splotch_status splotch_final_transform(float *a, int64_t count, void *stream);
 
 /* Test hook: per-particle raster outputs for one view, out8 = device float[8][n]:
  * X, Y, R, zc, e_r, e_g, e_b (emission = brightness x colour), active (0 / 1).

@@ -42,7 +42,7 @@ class CameraC(C.Structure):
 
 class RenderParamsC(C.Structure):
     _fields_ = [("tile", C.c_int32), ("rfac", C.c_float), ("sigma_over_R", C.c_float),
-                ("r_min_px", C.c_float), ("flags", C.c_int32)]
+                ("r_min_px", C.c_float), ("block_particles", C.c_int32), ("flags", C.c_int32)]
 
 
 class SplotchError(RuntimeError):
@@ -77,6 +77,7 @@ SIGNATURES = {
     "splotch_plan_destroy": ([C.c_void_p], C.c_int),
     "splotch_workspace_bytes": ([C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int64], C.c_int64),
     "splotch_selftest_bounded_wait": ([C.c_int64, C.c_void_p], C.c_int),
+    "splotch_final_transform": ([C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "splotch_last_timing": ([C.c_void_p, C.c_void_p], C.c_int),
     "splotch_status_string": ([C.c_int], C.c_char_p),
     "splotch_last_error": ([], C.c_char_p),

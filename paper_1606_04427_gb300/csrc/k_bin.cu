@@ -131,28 +131,32 @@ __global__ void __launch_bounds__(kThreads) k_count(SceneDev sc, FrameDev fr) {
     if (threadIdx.x < g_n) s_view[threadIdx.x] = fr.views[v0 + threadIdx.x];
     __syncthreads();
 
-    constexpr int VEC = Store<S>::VEC;
     const int64_t s = (int64_t)b * fr.chunk;
     const int64_t e = min(sc.n, s + fr.chunk);
-    for (int64_t i = s + (int64_t)threadIdx.x * VEC; i < e; i += (int64_t)blockDim.x * VEC) {
-        float x[VEC], y[VEC], z[VEC], h[VEC];
-        Store<S>::load(sc.x, i, x);
-        Store<S>::load(sc.y, i, y);
-        Store<S>::load(sc.z, i, z);
-        Store<S>::load(sc.h, i, h);
+    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
+        const float x = load1<S>(sc.x, i), y = load1<S>(sc.y, i), z = load1<S>(sc.z, i), h = load1<S>(sc.h, i);
         for (int g = 0; g < g_n; ++g) {
             const ViewParams &vp = s_view[g];
+            Raster r;
+            if (!raster_one(vp, x, y, z, h, r)) continue;
             int *hist = s_hist + g * nt;
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) {
-                Raster r;
-                if (i + k < e && raster_one(vp, x[k], y[k], z[k], h[k], r)) {
-                    const int tx0 = r.i0 / vp.T, tx1 = r.i1 / vp.T;
-                    const int ty0 = r.j0 / vp.T, ty1 = r.j1 / vp.T;
-                    for (int ty = ty0; ty <= ty1; ++ty)
-                        for (int tx = tx0; tx <= tx1; ++tx)
-                            if (tile_member(vp, r.X, r.Y, r.R, tx, ty)) atomicAdd(&hist[ty * vp.ntx + tx], 1);
-                }
+            const int tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
+            const int ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
+            if (tx1 - tx0 <= 1 && ty1 - ty0 <= 1) {
+                // at most 2 x 2 candidate tiles: the common case, tested without loops
+                const bool m00 = tile_member(vp, r.X, r.Y, r.R, tx0, ty0);
+                const bool m10 = tx1 > tx0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty0);
+                const bool m01 = ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx0, ty1);
+                const bool m11 = tx1 > tx0 && ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty1);
+                const int t00 = ty0 * vp.ntx + tx0;
+                if (m00) atomicAdd(&hist[t00], 1);
+                if (m10) atomicAdd(&hist[t00 + 1], 1);
+                if (m01) atomicAdd(&hist[t00 + vp.ntx], 1);
+                if (m11) atomicAdd(&hist[t00 + vp.ntx + 1], 1);
+            } else {
+                for (int ty = ty0; ty <= ty1; ++ty)
+                    for (int tx = tx0; tx <= tx1; ++tx)
+                        if (tile_member(vp, r.X, r.Y, r.R, tx, ty)) atomicAdd(&hist[ty * vp.ntx + tx], 1);
             }
         }
     }
@@ -330,41 +334,46 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
     for (int k = threadIdx.x; k <= sc.n_types; k += blockDim.x) s_tb[k] = sc.type_begin[k];
     __syncthreads();
 
-    constexpr int VEC = Store<S>::VEC;
     const int64_t s = (int64_t)b * fr.chunk;
     const int64_t e = min(sc.n, s + fr.chunk);
     int type = 0;
-    for (int64_t i = s + (int64_t)threadIdx.x * VEC; i < e; i += (int64_t)blockDim.x * VEC) {
-        float x[VEC], y[VEC], z[VEC], h[VEC], it[VEC];
-        Store<S>::load(sc.x, i, x);
-        Store<S>::load(sc.y, i, y);
-        Store<S>::load(sc.z, i, z);
-        Store<S>::load(sc.h, i, h);
-        Store<S>::load(sc.it, i, it);
+    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
+        const float x = load1<S>(sc.x, i), y = load1<S>(sc.y, i), z = load1<S>(sc.z, i), h = load1<S>(sc.h, i);
+        const float itn = load1<S>(sc.it, i);
+        while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
+        uint32_t q = __float2uint_rn(__fmul_rn(itn, (float)kCodeMax));
+        q = min(q, kCodeMax);
+        const float code = __uint_as_float(((uint32_t)type << 24) | q);
         for (int g = 0; g < g_n; ++g) {
             const ViewParams &vp = s_view[g];
+            Raster r;
+            if (!raster_one(vp, x, y, z, h, r)) continue;
             int *cur = s_cur + g * nt;
             const int64_t *seg = fr.offsets + (int64_t)(v0 + g) * nt;
+            const float4 rec = make_float4(r.X, r.Y, r.R, code);
+            const int tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
+            const int ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
+            if (tx1 - tx0 <= 1 && ty1 - ty0 <= 1) {
+                const int t00 = ty0 * vp.ntx + tx0;
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) {
-                Raster r;
-                if (i + k < e && raster_one(vp, x[k], y[k], z[k], h[k], r)) {
-                    while (type + 1 < sc.n_types && i + k >= s_tb[type + 1]) ++type;
-                    uint32_t q = __float2uint_rn(__fmul_rn(it[k], (float)kCodeMax));
-                    q = min(q, kCodeMax);
-                    const float4 rec = make_float4(r.X, r.Y, r.R, __uint_as_float(((uint32_t)type << 24) | q));
-                    const int tx0 = r.i0 / vp.T, tx1 = r.i1 / vp.T;
-                    const int ty0 = r.j0 / vp.T, ty1 = r.j1 / vp.T;
-                    for (int ty = ty0; ty <= ty1; ++ty)
-                        for (int tx = tx0; tx <= tx1; ++tx)
-                            if (tile_member(vp, r.X, r.Y, r.R, tx, ty)) {
-                                const int t = ty * vp.ntx + tx;
-                                const int loc = atomicAdd(&cur[t], 1);
-                                const int64_t pos = seg[t] + loc;
-                                fr.lists[pos] = rec;
-                                if (fr.pids) fr.pids[pos] = (int)(i + k);
-                            }
+                for (int qd = 0; qd < 4; ++qd) {
+                    const int dx = qd & 1, dy = qd >> 1;
+                    if ((dx && tx1 == tx0) || (dy && ty1 == ty0)) continue;
+                    if (!tile_member(vp, r.X, r.Y, r.R, tx0 + dx, ty0 + dy)) continue;
+                    const int t = t00 + dy * vp.ntx + dx;
+                    const int64_t pos = seg[t] + atomicAdd(&cur[t], 1);
+                    fr.lists[pos] = rec;
+                    if (fr.pids) fr.pids[pos] = (int)i;
                 }
+            } else {
+                for (int ty = ty0; ty <= ty1; ++ty)
+                    for (int tx = tx0; tx <= tx1; ++tx)
+                        if (tile_member(vp, r.X, r.Y, r.R, tx, ty)) {
+                            const int t = ty * vp.ntx + tx;
+                            const int64_t pos = seg[t] + atomicAdd(&cur[t], 1);
+                            fr.lists[pos] = rec;
+                            if (fr.pids) fr.pids[pos] = (int)i;
+                        }
             }
         }
     }

@@ -198,6 +198,7 @@ extern "C" splotch_render_params splotch_default_params(void) {
     p.rfac = 0.75f;
     p.sigma_over_R = 0.5f;
     p.r_min_px = 0.75f;
+    p.block_particles = 0;
     p.flags = 0;
     return p;
 }
@@ -474,6 +475,7 @@ static splotch_status check_params(const splotch_render_params *pr) {
         return fail(SPLOTCH_ERR_INVALID_ARG, "sigma_over_R <= 0");
     if (!(pr->r_min_px >= 0.0f) || !std::isfinite(pr->r_min_px)) return fail(SPLOTCH_ERR_INVALID_ARG, "r_min_px < 0");
     if (pr->tile < 0 || pr->tile > kMaxTile) return fail(SPLOTCH_ERR_INVALID_ARG, "tile outside 0..%d", kMaxTile);
+    if (pr->block_particles < 0) return fail(SPLOTCH_ERR_INVALID_ARG, "block_particles < 0");
     return SPLOTCH_OK;
 }
 
@@ -516,6 +518,8 @@ static splotch_status make_view(const splotch_camera *c, const splotch_render_pa
     v.ntx = (c->width + T - 1) / T;
     v.nty = (c->height + T - 1) / T;
     v.n_tiles = v.ntx * v.nty;
+    v.fastdiv = (T > 1 && c->width <= 65536 && c->height <= 65536) ? 1 : 0;
+    v.tmagic = T > 1 ? (uint32_t)((((uint64_t)1) << 32) / (uint64_t)T + 1) : 0u;
     return SPLOTCH_OK;
 }
 
@@ -537,7 +541,8 @@ struct FrameHost {
 
 static const int64_t kRelBudget = 256ll << 20;
 
-static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_tiles, int T) {
+static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_tiles, int T,
+                         int block_particles = 0) {
     fh.V = V;
     fh.T = T;
     fh.n_tiles = n_tiles;
@@ -552,6 +557,7 @@ static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_ti
     target = std::min(target, n_units);
     const int64_t max_chunks = std::max<int64_t>(1, kRelBudget / (4ll * V * n_tiles));
     int64_t nch = std::min(target, max_chunks);
+    if (block_particles > 0) nch = std::min(max_chunks, std::max<int64_t>(1, (sc->n + block_particles - 1) / block_particles));
     const int64_t upc = (n_units + nch - 1) / nch;
     fh.chunk = upc * unit;
     fh.n_chunks = (int)std::max<int64_t>(1, (sc->n + fh.chunk - 1) / fh.chunk);
@@ -690,7 +696,7 @@ static splotch_status render_frame(splotch_scene *sc, const RenderSetup &rs, flo
                                    bool sync, bool want_pids, int32_t *dbg_counts, int64_t *dbg_offsets,
                                    int32_t *dbg_members, int64_t dbg_cap, int64_t *dbg_total) {
     FrameHost fh;
-    layout_fixed(fh, sc, rs.V, rs.views[0].n_tiles, rs.T);
+    layout_fixed(fh, sc, rs.V, rs.views[0].n_tiles, rs.T, rs.pr.block_particles);
     const bool timed = (rs.pr.flags & SPLOTCH_TIMING) != 0 && !dbg_members;
     cudaEvent_t *ev = nullptr;
     if (timed) {
@@ -887,7 +893,7 @@ extern "C" splotch_status splotch_plan_create(splotch_scene *sc, const splotch_c
         return s;
     }
     pl->use_graph = (pl->rs.pr.flags & SPLOTCH_PLAN_GRAPH) != 0;
-    layout_fixed(pl->fh, sc, pl->rs.V, pl->rs.views[0].n_tiles, pl->rs.T);
+    layout_fixed(pl->fh, sc, pl->rs.V, pl->rs.views[0].n_tiles, pl->rs.T, pl->rs.pr.block_particles);
     pl->fixed = (char *)sc->mem.alloc(pl->fh.fixed_bytes, st);
     if (!pl->fixed) {
         delete pl;
@@ -1012,4 +1018,10 @@ extern "C" splotch_status splotch_selftest_bounded_wait(int64_t limit_cycles, vo
     if (r == 2) return fail(SPLOTCH_ERR_TIMEOUT, "bounded wait gave up after %lld cycles", (long long)limit_cycles);
     if (r == 1) return SPLOTCH_OK;
     return fail(SPLOTCH_ERR_CUDA, "selftest kernel did not report");
+}
+
+extern "C" splotch_status splotch_final_transform(float *a, int64_t count, void *stream) {
+    if (count < 0 || (count > 0 && !a)) return fail(SPLOTCH_ERR_INVALID_ARG, "bad buffer");
+    CUDA_TRY(launch_final(a, count, (cudaStream_t)stream));
+    return SPLOTCH_OK;
 }

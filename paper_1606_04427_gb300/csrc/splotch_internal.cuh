@@ -35,7 +35,15 @@ struct ViewParams {
     float kexp;           // -log2(e) / sigma_over_R^2: w = exp2(d2 * kexp / R^2)
     float hd;             // 0.70710677 * T, rounded once
     int W, H, T, ntx, nty, n_tiles;
+    uint32_t tmagic;      // floor(2^32 / T) + 1: pixel -> tile index by one multiply-high
+    int fastdiv;          // 1 when W, H <= 65536 and T > 1 (the multiply-high is exact there)
 };
+
+// Tile index of a pixel coordinate (>= 0): q = floor(p / T).  For p < 2^16 and T <= 64 the
+// product p * (floor(2^32 / T) + 1) / 2^32 errs by less than 2^-16 < 1 / T, so the floor is exact.
+__device__ __forceinline__ int tile_of(const ViewParams &v, int p) {
+    return v.fastdiv ? (int)__umulhi((unsigned)p, v.tmagic) : p / v.T;
+}
 
 // Device-resident scene as the kernels see it.
 struct SceneDev {
@@ -112,6 +120,18 @@ template <> struct Store<2> {
         }
     }
 };
+
+// One attribute of one particle (a warp reads 32 consecutive particles: coalesced).
+template <int S> __device__ __forceinline__ float load1(const void *p, int64_t i);
+template <> __device__ __forceinline__ float load1<0>(const void *p, int64_t i) {
+    return __ldg(static_cast<const float *>(p) + i);
+}
+template <> __device__ __forceinline__ float load1<1>(const void *p, int64_t i) {
+    return __half2float(__ldg(static_cast<const __half *>(p) + i));
+}
+template <> __device__ __forceinline__ float load1<2>(const void *p, int64_t i) {
+    return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(p) + i));
+}
 
 // ------------------------------------------------------------------------------------
 // Raster rule (FP32, each operation rounded once, left to right).
@@ -236,6 +256,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
+// 2^x on the SFU (PTX ex2.approx.ftz, max relative error about 2^-22); the weights it feeds
+// are values, never decisions.
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ------------------------------------------------------------------------------------
 // Host-side launchers (defined in the kernel translation units).
 
@@ -254,6 +282,7 @@ cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, flo
 int splat_blocks_per_sm(int T);
 size_t splat_smem_bytes(int T);
 cudaError_t launch_selftest_wait(long long limit, int *result, cudaStream_t st);
+cudaError_t launch_final(float *a, int64_t count, cudaStream_t st);
 cudaError_t launch_debug_raster(int storage, const SceneDev &sc, const ViewParams *view,
                                 float *out8, cudaStream_t st);
 

@@ -26,6 +26,7 @@ class RenderParams:
     rfac: float = 0.75
     sigma_over_R: float = 0.5
     r_min_px: float = 0.75
+    block_particles: int = 0
     accum: bool = False
     sync: bool = False
     graph: bool = False
@@ -37,6 +38,7 @@ class RenderParams:
         p.rfac = float(self.rfac)
         p.sigma_over_R = float(self.sigma_over_R)
         p.r_min_px = float(self.r_min_px)
+        p.block_particles = int(self.block_particles)
         p.flags = ((_lib.OUT_ACCUM if self.accum else 0) | (_lib.SYNC if self.sync else 0)
                    | (_lib.PLAN_GRAPH if self.graph else 0) | (_lib.TIMING if self.timing else 0))
         return p

@@ -41,7 +41,7 @@ def test_status_strings_and_defaults(lib):
         assert lib.splotch_status_string(s)
     assert b"unknown" in lib.splotch_status_string(99)
     p = lib.splotch_default_params()
-    assert (p.tile, p.rfac, p.sigma_over_R, p.r_min_px, p.flags) == (0, 0.75, 0.5, 0.75, 0)
+    assert (p.tile, p.rfac, p.sigma_over_R, p.r_min_px, p.block_particles, p.flags) == (0, 0.75, 0.5, 0.75, 0, 0)
 
 
 def _lib_camera(lib, cam):

@@ -1,0 +1,120 @@
+"""Batched, served and sharded modes on the GPU, against the single-view path and the
+oracle (needs a GB300)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1606_04427_gb300 import _lib, autotune, build, render, serve, shard, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def test_autotune_picks_a_candidate_and_caches_it(tmp_path):
+    ps = synth.clustered_set(40000, 3, grid=64).with_brightness([0.05])
+    sc = render.Scene(ps, "f16")
+    cams = synth.orbit_cameras(4, 128, 96)
+    cache = str(tmp_path / "tune.json")
+    res = autotune.tune(sc, cams, tiles=(8, 16, 32), blocks=(0, 8192), repeats=2, cache_path=cache)
+    assert res["params"].tile in (8, 16, 32) and not res["cached"]
+    assert len([r for r in res["table"] if "ms" in r]) == 6
+    again = autotune.tune(sc, cams, tiles=(8, 16, 32), blocks=(0, 8192), cache_path=cache)
+    assert again["cached"] and again["params"].tile == res["params"].tile
+    with open(cache) as f:
+        assert res["key"] in json.load(f)
+    # the tuned plan still renders the oracle's image
+    plan = render.Plan(sc, cams, res["params"], graph=True)
+    out = plan.new_output()
+    plan.launch(out)
+    plan.check()
+    for v, cam in enumerate(cams):
+        ref = oracle.final(oracle.render(ps, cam, oracle.Params(tile=res["params"].tile), "f16"))
+        assert np.abs(out[v].cpu().numpy() - ref).max() <= 2e-3
+
+
+def test_block_particles_do_not_change_the_image():
+    ps = synth.clustered_set(50000, 7, grid=64).with_brightness([0.05])
+    sc = render.Scene(ps, "f32")
+    cam = synth.front_camera(160, 120)
+    base = sc.render(cam).cpu().numpy()
+    for bp in (1024, 5000, 40000):
+        other = sc.render(cam, render.RenderParams(block_particles=bp)).cpu().numpy()
+        assert np.abs(base - other).max() <= 1e-4
+
+
+def _served_sets():
+    rng = np.random.default_rng(12)
+    sets = [synth.clustered_set(n, 20 + k, grid=32).with_brightness([b])
+            for k, (n, b) in enumerate([(20000, 0.2), (60000, 0.07), (150000, 0.03)])]
+    reqs = []
+    t = 0.0
+    for i in range(18):
+        t += rng.exponential(0.002)
+        cam = synth.random_camera(rng, sizes=(64, 96, 160, 256))
+        reqs.append(synth.Request(int(rng.integers(0, 3)), cam, t))
+    return sets, reqs
+
+
+def test_server_result_alone_equals_result_in_the_mix():
+    sets, reqs = _served_sets()
+    scenes = [render.Scene(p, "f16") for p in sets]
+    alone = [scenes[r.set_index].render(r.camera, render.RenderParams(sync=True)).cpu().numpy() for r in reqs]
+    srv = serve.Server(scenes, slots=3, keep_images=True)
+    try:
+        st = srv.run_trace(reqs)
+    finally:
+        srv.close()
+    assert not srv.errors, srv.errors
+    assert st["requests"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
+    by_id = {d.request_id: d for d in srv.done}
+    assert max(d.finish for d in srv.done) > 0
+    for i, r in enumerate(reqs):
+        img = by_id[i].image.cpu().numpy()
+        assert np.abs(img - alone[i]).max() <= 1e-4, i
+        ref = oracle.final(oracle.render(sets[r.set_index], r.camera, oracle.Params(), "f16"))
+        assert np.abs(img - ref).max() <= 2e-3, i
+
+
+def test_server_admission_by_footprint():
+    """With a budget smaller than any request the server still drains the queue, one
+    request in flight at a time; with a large budget requests overlap."""
+    sets, reqs = _served_sets()
+    scenes = [render.Scene(p, "f16") for p in sets]
+    srv = serve.Server(scenes, slots=4, hbm_budget=1)
+    inflight = []
+    try:
+        for r in reqs:
+            srv.submit(r.set_index, r.camera)
+        while srv.queue or srv.in_flight:
+            inflight.append(srv.in_flight)
+            torch.cuda.synchronize()
+        srv.wait_all(timeout=120)
+    finally:
+        srv.close()
+    assert len(srv.done) == len(reqs) and not srv.errors
+    assert max(inflight) <= 1
+    assert all(d.reserved_bytes > 0 for d in srv.done)
+
+
+def test_shards_sum_to_the_whole_frame():
+    """Linearity of the accumulation: rendering two particle shards and summing equals
+    rendering all of them (the multi-GPU exchange, checked on one GPU)."""
+    ps = synth.two_species_set(30000, 10000, 8, grid=32).with_brightness([0.05, 0.3])
+    cam = synth.front_camera(120, 100)
+    whole = render.Scene(ps, "f32").render(cam, render.RenderParams(accum=True))
+    parts = [render.Scene(shard.shard_particles(ps, r, 3), "f32").render(cam, render.RenderParams(accum=True))
+             for r in range(3)]
+    summed = parts[0] + parts[1] + parts[2]
+    assert torch.allclose(summed, whole, rtol=2e-5, atol=1e-7)
+    shard.final_transform_(summed)
+    ref = oracle.final(oracle.render(ps, cam))
+    assert np.abs(summed.cpu().numpy() - ref).max() <= 1e-4
