@@ -9,31 +9,26 @@
 // item is a tile, or a K-record slice of a crowded tile (so dense clusters do not
 // serialise on one CTA).  The item's records are staged from HBM into shared memory by
 // bulk copies (cp.async.bulk, double buffered, mbarrier completion with a bounded wait).
-// Each stage is rendered in two phases:
-//   A. small records (support < kBigR px): warps take 32 records at a time, enumerate
-//      their (record, pixel row) pairs across lanes with a warp scan, and add e * w to
-//      an FP32 tile accumulator in shared memory with atomic adds;
-//   B. large records (support >= kBigR px, which carry most of the covered pixels):
-//      each warp owns a band of 8 x 4 pixel blocks of the tile, one pixel per lane per
-//      block, and gathers every large record over the blocks it overlaps into registers
-//      (no atomics).
-// The register sums join the shared accumulator at the end of the item.  The epilogue
-// writes 1 - exp(-a) for the tile; slices of a split tile add their partial sums into a
-// scratch tile and the last slice to finish writes the result.
+//
+// Pixel ownership goes one level further than the paper's thread-per-tile: the tile is
+// cut into 8 x 4 pixel blocks, block row r belongs to warp r mod 8, and each lane owns
+// one pixel of each of its warp's blocks, accumulating it in registers.  Per stage:
+//   1. decode: one lane per record computes the record's pixel box inside the tile, its
+//      colour (brightness x colormap) and Gaussian scale, and appends the record to the
+//      list of every warp owning a block row the box meets;
+//   2. gather: each warp walks its list; for every block of its own that the box
+//      overlaps, each lane tests its pixel with the FP32 coverage rule and adds e * w
+//      to its registers.  No atomics: a pixel has exactly one owner.
+// In clustered data most pixels receive hundreds of contributions per frame, where a
+// shared-memory scatter would serialise on atomic conflicts.  At the end of the item the
+// lanes write 1 - exp(-a) for their pixels; slices of a split tile add their partial
+// sums into a scratch tile and the last slice to finish writes the result.
 #include "splotch_internal.cuh"
 
 namespace spl {
 
-constexpr float kBigR = 3.5f;
-
-struct __align__(16) Slot {  // small record being enumerated by a warp
-    float X, Y, R2, kr;
-    float er, eg, eb, eps;
-    int ilo, ihi, jlo, excl;
-};
-
-struct __align__(16) Big {  // large record queued for the register gather
-    int ilo, ihi, jlo, jhi;
+struct __align__(16) Rec {
+    int ilo, ihi, jlo, jhi;  // tile-local box
     float X, Y, R2, kr;
     float er, eg, eb, pad;
 };
@@ -47,34 +42,28 @@ __device__ __forceinline__ int find_tile(const int *__restrict__ item_off, int N
     return a;
 }
 
-__host__ __device__ __forceinline__ int acc_plane(int T) { return T * (T + 1) + 1; }
-
-// 8 x 4 pixel blocks per warp for tile edge T (8 warps share ceil(T/8) * ceil(T/4) blocks)
+// blocks of 8 x 4 pixels; warp w owns block rows w, w + 8, ...; NB blocks per warp
 __host__ __device__ __forceinline__ int blocks_per_warp(int T) {
-    return (((T + 7) >> 3) * ((T + 3) >> 2) + kSplatWarps - 1) / kSplatWarps;
+    const int bxn = (T + 7) >> 3, byn = (T + 3) >> 2;
+    return bxn * ((byn + kSplatWarps - 1) / kSplatWarps);
 }
 
-size_t splat_smem_bytes(int T) {
-    return sizeof(float4) * 2 * kStage + sizeof(Slot) * kSplatWarps * 32 + sizeof(Big) * kStage +
-           sizeof(short) * kSplatWarps * kStage + sizeof(float) * 3 * (size_t)acc_plane(T);
+size_t splat_smem_bytes(int) {
+    return sizeof(float4) * 2 * kStage + sizeof(Rec) * kStage + sizeof(short) * kSplatWarps * kStage;
 }
 
 template <int NB>
-__global__ void __launch_bounds__(kSplatThreads, 2) k_splat(SceneDev sc, FrameDev fr, int *queue, float *out,
+__global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDev fr, int *queue, float *out,
                                                          int out_accum) {
     if (fr.status[kStatOverflow]) return;
     extern __shared__ __align__(16) unsigned char s_raw[];
     __shared__ uint64_t s_bar[2];
-    __shared__ int s_item, s_last, s_nbig;
-    __shared__ int s_next[2];
-    __shared__ int s_wcnt[kSplatWarps];              // large records queued per warp band
-    __shared__ int s_band[kSplatWarps][2];           // tile-local rows of each warp's blocks
+    __shared__ int s_item, s_last;
+    __shared__ int s_wcnt[kSplatWarps];
 
-    float4 *s_buf = reinterpret_cast<float4 *>(s_raw);                   // [2][kStage]
-    Slot *s_slot = reinterpret_cast<Slot *>(s_buf + 2 * kStage);          // [warps][32]
-    Big *s_big = reinterpret_cast<Big *>(s_slot + kSplatWarps * 32);      // [kStage]
-    short *s_wlist = reinterpret_cast<short *>(s_big + kStage);           // [warps][kStage]
-    float *s_acc = reinterpret_cast<float *>(s_wlist + kSplatWarps * kStage);  // [3][plane]
+    float4 *s_buf = reinterpret_cast<float4 *>(s_raw);             // [2][kStage]
+    Rec *s_rec = reinterpret_cast<Rec *>(s_buf + 2 * kStage);       // [kStage]
+    short *s_wl = reinterpret_cast<short *>(s_rec + kStage);        // [warps][kStage]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt = fr.n_tiles;
@@ -83,38 +72,25 @@ __global__ void __launch_bounds__(kSplatThreads, 2) k_splat(SceneDev sc, FrameDe
     const int64_t K = fr.sizes[kSizeK];
     const ViewParams g0 = fr.views[0];
     const int T = g0.T, W = g0.W, H = g0.H, ntx = g0.ntx;
-    const int plane = acc_plane(T);
-    const int stride = T + 1;
-
-    // this warp's register blocks (tile-local origins), identical for every item
-    const int bxn = (T + 7) >> 3, nbt = bxn * ((T + 3) >> 2);
-    const int nbw = blocks_per_warp(T);
+    const int bxn = (T + 7) >> 3, byn = (T + 3) >> 2;
     const int lc = lane & 7, lr = lane >> 3;
+
+    // this warp's blocks: tile-local origins (empty blocks get an origin beyond the tile)
     int bcol[NB], brow[NB];
-    int band_lo = 1 << 30, band_hi = -(1 << 30);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const int k = warp * nbw + b;
-        const bool ok = b < nbw && k < nbt;
-        bcol[b] = ok ? (k % bxn) * 8 : 1 << 28;
-        brow[b] = ok ? (k / bxn) * 4 : 1 << 28;
-        if (ok) {
-            band_lo = min(band_lo, brow[b]);
-            band_hi = max(band_hi, brow[b] + 3);
-        }
+        const int br = warp + kSplatWarps * (b / bxn), bc = b % bxn;
+        const bool ok = b < bxn * ((byn + kSplatWarps - 1) / kSplatWarps) && br < byn;
+        bcol[b] = ok ? bc * 8 : 1 << 20;
+        brow[b] = ok ? br * 4 : 1 << 20;
     }
 
-    if (lane == 0) {
-        s_band[warp][0] = band_lo;
-        s_band[warp][1] = band_hi;
-        s_wcnt[warp] = 0;
-    }
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         mbar_fence_init();
-        s_nbig = 0;
     }
+    if (tid < kSplatWarps) s_wcnt[tid] = 0;
     __syncthreads();
     uint32_t phase0 = 0, phase1 = 0;
 
@@ -138,30 +114,29 @@ __global__ void __launch_bounds__(kSplatThreads, 2) k_splat(SceneDev sc, FrameDe
         const int nrec = (int)(min(seg1, e0 + K) - e0);
         const int nst = (nrec + kStage - 1) / kStage;
 
-        float ar[NB], ag[NB], ab[NB];
-        unsigned pvalid = 0;  // bit b: this lane's pixel of block b lies in the tile and image
+        // this lane's pixel in each block: centre coordinates and accumulators
+        float fx[NB], fy[NB], ar[NB], ag[NB], ab[NB];
+        unsigned pvalid = 0;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
+            fx[b] = (float)(px0 + bcol[b] + lc) + 0.5f;
+            fy[b] = (float)(py0 + brow[b] + lr) + 0.5f;
             ar[b] = ag[b] = ab[b] = 0.0f;
             if (bcol[b] + lc < tw && brow[b] + lr < th) pvalid |= 1u << b;
         }
 
-        for (int k = tid; k < 3 * plane; k += kSplatThreads) s_acc[k] = 0.0f;
-        if (tid == 0) s_next[0] = s_next[1] = 0;
         if (tid == 0 && nrec > 0) {
             const int c0 = min(kStage, nrec);
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&s_bar[0], (uint32_t)c0 * 16u);
             bulk_g2s(s_buf, fr.lists + e0, (uint32_t)c0 * 16u, &s_bar[0]);
         }
-        __syncthreads();
 
         for (int si = 0; si < nst; ++si) {
             const int cb = si & 1;
             if (tid == 0 && si + 1 < nst) {
                 const int nb = (si + 1) & 1;
                 const int cn = min(kStage, nrec - (si + 1) * kStage);
-                s_next[nb] = 0;
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&s_bar[nb], (uint32_t)cn * 16u);
                 bulk_g2s(s_buf + nb * kStage, fr.lists + e0 + (int64_t)(si + 1) * kStage,
@@ -175,124 +150,75 @@ __global__ void __launch_bounds__(kSplatThreads, 2) k_splat(SceneDev sc, FrameDe
             }
             const int cnt = min(kStage, nrec - si * kStage);
             const float4 *recs = s_buf + cb * kStage;
-            Slot *sl = s_slot + warp * 32;
 
-            // ---- phase A: decode, queue large records, splat small ones -------------------
-            const int ngroups = (cnt + 31) >> 5;
-            for (;;) {
-                int g = 0;
-                if (lane == 0) g = atomicAdd(&s_next[cb], 1);
-                g = __shfl_sync(0xffffffffu, g, 0);
-                if (g >= ngroups) break;
-                const int idx = g * 32 + lane;
-                int nrows = 0;
-                Slot me;
-                if (idx < cnt) {
-                    const float4 rec = recs[idx];
-                    const float X = rec.x, Y = rec.y, R = rec.z;
-                    const uint32_t code = __float_as_uint(rec.w);
-                    // tight pixel range of the support inside the tile; eps exceeds the FP32
-                    // rounding of X +- R at any position, so no covered pixel is left out
-                    const float eps = 1e-3f + 2e-6f * (fabsf(X) + fabsf(Y) + R);
-                    const int ilo = max(px0, (int)ceilf(clampf(X - R - 0.5f - eps, px0 - 1.0f, (float)(px0 + tw))));
-                    const int ihi = min(px0 + tw - 1, (int)floorf(clampf(X + R - 0.5f + eps, px0 - 1.0f, (float)(px0 + tw))));
-                    const int jlo = max(py0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))));
-                    const int jhi = min(py0 + th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))));
-                    const bool any = ilo <= ihi && jlo <= jhi;
-                    const int type = (int)(code >> 24);
-                    const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
-                    const int len = __ldg(&sc.lut_len[type]);
-                    const float f = It * (float)(len - 1);
-                    const int kk = min((int)f, len - 2);
-                    const float tau = f - (float)kk;
-                    const int lo = __ldg(&sc.lut_off[type]) + kk;
-                    const float4 c0 = __ldg(&sc.lut[lo]);
-                    const float4 c1 = __ldg(&sc.lut[lo + 1]);
-                    const float R2 = __fmul_rn(R, R);
-                    me.X = X; me.Y = Y; me.R2 = R2; me.kr = kexp / R2;
-                    me.er = (1.0f - tau) * c0.x + tau * c1.x;
-                    me.eg = (1.0f - tau) * c0.y + tau * c1.y;
-                    me.eb = (1.0f - tau) * c0.z + tau * c1.z;
-                    me.eps = eps;
-                    me.ilo = ilo; me.ihi = ihi; me.jlo = jlo;
-                    if (any && R >= kBigR) {
-                        Big q;
-                        q.ilo = ilo; q.ihi = ihi; q.jlo = jlo; q.jhi = jhi;
-                        q.X = X; q.Y = Y; q.R2 = R2; q.kr = me.kr;
-                        q.er = me.er; q.eg = me.eg; q.eb = me.eb; q.pad = 0.0f;
-                        const int slotq = atomicAdd(&s_nbig, 1);
-                        s_big[slotq] = q;
-                        // queue it to every warp whose band of rows it meets
-                        for (int w = 0; w < kSplatWarps; ++w) {
-                            if (jhi < py0 + s_band[w][0] || jlo > py0 + s_band[w][1]) continue;
-                            s_wlist[w * kStage + atomicAdd(&s_wcnt[w], 1)] = (short)slotq;
-                        }
-                    } else if (any) {
-                        nrows = jhi - jlo + 1;
-                    }
+            // ---- 1. decode; queue each record to the warps owning the block rows it meets
+            for (int idx = tid; idx < cnt; idx += kSplatThreads) {
+                const float4 rec = recs[idx];
+                const float X = rec.x, Y = rec.y, R = rec.z;
+                const uint32_t code = __float_as_uint(rec.w);
+                // tight pixel range of the support inside the tile; eps exceeds the FP32
+                // rounding of X +- R at any position, so no covered pixel is left out
+                const float eps = 1e-3f + 2e-6f * (fabsf(X) + fabsf(Y) + R);
+                const int ilo = max(px0, (int)ceilf(clampf(X - R - 0.5f - eps, px0 - 1.0f, (float)(px0 + tw))));
+                const int ihi = min(px0 + tw - 1, (int)floorf(clampf(X + R - 0.5f + eps, px0 - 1.0f, (float)(px0 + tw))));
+                const int jlo = max(py0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))));
+                const int jhi = min(py0 + th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))));
+                if (ilo > ihi || jlo > jhi) continue;
+                const int type = (int)(code >> 24);
+                const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
+                const int len = __ldg(&sc.lut_len[type]);
+                const float f = It * (float)(len - 1);
+                const int kk = min((int)f, len - 2);
+                const float tau = f - (float)kk;
+                const int lo = __ldg(&sc.lut_off[type]) + kk;
+                const float4 c0 = __ldg(&sc.lut[lo]);
+                const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                Rec q;
+                q.ilo = ilo - px0;
+                q.ihi = ihi - px0;
+                q.jlo = jlo - py0;
+                q.jhi = jhi - py0;
+                q.X = X;
+                q.Y = Y;
+                q.R2 = __fmul_rn(R, R);
+                q.kr = __fdividef(kexp, q.R2);
+                q.er = (1.0f - tau) * c0.x + tau * c1.x;
+                q.eg = (1.0f - tau) * c0.y + tau * c1.y;
+                q.eb = (1.0f - tau) * c0.z + tau * c1.z;
+                q.pad = 0.0f;
+                s_rec[idx] = q;
+                const int br0 = q.jlo >> 2, br1 = q.jhi >> 2;
+                const int nw = min(br1 - br0 + 1, kSplatWarps);
+                for (int k = 0; k < nw; ++k) {
+                    const int w = (br0 + k) & (kSplatWarps - 1);
+                    s_wl[w * kStage + atomicAdd(&s_wcnt[w], 1)] = (short)idx;
                 }
-                const int incl = warp_incl_scan_i(nrows);
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                if (total == 0) continue;
-                if (nrows) {
-                    me.excl = incl - nrows;
-                    sl[lane] = me;
-                }
-                __syncwarp();
-                for (int base = 0; base < total; base += 32) {
-                    const int it = base + lane;
-                    const int itc = min(it, total - 1);
-                    int l = 0;
-#pragma unroll
-                    for (int st = 16; st; st >>= 1) {
-                        const int cand = __shfl_sync(0xffffffffu, incl, l + st - 1);
-                        if (cand <= itc) l += st;
-                    }
-                    if (it < total) {
-                        const Slot P = sl[l];
-                        const int row = P.jlo + (it - P.excl);
-                        const float dy = __fsub_rn(__fadd_rn((float)row, 0.5f), P.Y);
-                        const float dy2 = __fmul_rn(dy, dy);
-                        // columns where dx^2 < R^2 - dy^2, widened by the rounding margin; the
-                        // exact FP32 test below still decides every pixel
-                        const float rem = fmaxf(P.R2 - dy2, 0.0f) + P.R2 * 4e-7f + 1e-12f;
-                        const float half = rem * rsqrtf(rem + 1e-30f);
-                        const float wide = half + P.eps;
-                        const int a = max(P.ilo, (int)ceilf(clampf(P.X - 0.5f - wide, P.ilo - 1.0f, P.ihi + 1.0f)));
-                        const int b = min(P.ihi, (int)floorf(clampf(P.X - 0.5f + wide, P.ilo - 1.0f, P.ihi + 1.0f)));
-                        float *acc = s_acc + (row - py0) * stride - px0;
-                        float fi = (float)a + 0.5f;
-                        for (int i = a; i <= b; ++i, fi += 1.0f) {
-                            const float dx = __fsub_rn(fi, P.X);
-                            const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2);
-                            if (d2 < P.R2) {
-                                const float w = ex2_fast(d2 * P.kr);
-                                atomicAdd(acc + i, P.er * w);
-                                atomicAdd(acc + plane + i, P.eg * w);
-                                atomicAdd(acc + 2 * plane + i, P.eb * w);
-                            }
-                        }
-                    }
-                }
-                __syncwarp();
             }
             __syncthreads();
 
-            // ---- phase B: register gather of the large records over this warp's blocks ------
+            // ---- 2. gather: this warp's list over this warp's blocks ---------------------
+            // blocks b = rr * bxn + bc: block row rr of this warp (tile rows brow), column bc
             const int nmine = s_wcnt[warp];
-            const short *mine = s_wlist + warp * kStage;
+            const short *mine = s_wl + warp * kStage;
             for (int k = 0; k < nmine; ++k) {
-                const Big *bq = &s_big[mine[k]];
-                const int4 box = *reinterpret_cast<const int4 *>(&bq->ilo);
-                const float4 pa = *reinterpret_cast<const float4 *>(&bq->X);
-                const float4 pb = *reinterpret_cast<const float4 *>(&bq->er);
+                const Rec *q = &s_rec[mine[k]];
+                const int4 box = *reinterpret_cast<const int4 *>(&q->ilo);
+                const float4 pa = *reinterpret_cast<const float4 *>(&q->X);
+                const float4 pb = *reinterpret_cast<const float4 *>(&q->er);
+                const int bc_lo = box.x >> 3, bc_hi = box.y >> 3;  // overlapped block columns
+                // rows of this warp's blocks repeat every bxn blocks: one dy^2 per block row
+                float dy2[NB];
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
-                    const int c0 = px0 + bcol[b], r0 = py0 + brow[b];
-                    if (c0 > box.y || c0 + 7 < box.x || r0 > box.w || r0 + 3 < box.z) continue;
-                    const float dx = __fsub_rn((float)(c0 + lc) + 0.5f, pa.x);
-                    const float dy = __fsub_rn((float)(r0 + lr) + 0.5f, pa.y);
-                    const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+                    const float dy = __fsub_rn(fy[b], pa.y);
+                    dy2[b] = __fmul_rn(dy, dy);
+                }
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int bc = bcol[b] >> 3;
+                    if (bc < bc_lo || bc > bc_hi || brow[b] > box.w || brow[b] + 3 < box.z) continue;
+                    const float dx = __fsub_rn(fx[b], pa.x);
+                    const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2[b]);
                     if (((pvalid >> b) & 1u) && d2 < pa.z) {
                         const float w = ex2_fast(d2 * pa.w);
                         ar[b] += pb.x * w;
@@ -302,39 +228,29 @@ __global__ void __launch_bounds__(kSplatThreads, 2) k_splat(SceneDev sc, FrameDe
                 }
             }
             __syncthreads();
-            if (tid == 0) s_nbig = 0;
-            if (lane == 0) s_wcnt[warp] = 0;
+            if (tid < kSplatWarps) s_wcnt[tid] = 0;
         }
 
-        // register sums join the shared accumulator (each pixel has exactly one owner lane)
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            if ((pvalid >> b) & 1u) {
-                const int o = (brow[b] + lr) * stride + bcol[b] + lc;
-                s_acc[o] += ar[b];
-                s_acc[plane + o] += ag[b];
-                s_acc[2 * plane + o] += ab[b];
-            }
-        }
-        __syncthreads();
-
-        // epilogue: final transform of the tile, or merge of a split tile's slices
+        // epilogue: final transform of this lane's pixels, or merge of a split tile
         float *o = out + (int64_t)v * H * W * 3;
-        const int rowlen = 3 * tw;
         if (slot < 0) {
-            for (int k = tid; k < th * rowlen; k += kSplatThreads) {
-                const int r = k / rowlen, cc = k - r * rowlen;
-                const int col = cc / 3, ch = cc - col * 3;
-                const float a = s_acc[ch * plane + r * stride + col];
-                o[((int64_t)(py0 + r) * W + px0) * 3 + cc] = out_accum ? a : -expm1f(-a);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (!((pvalid >> b) & 1u)) continue;
+                float *p = o + ((int64_t)(py0 + brow[b] + lr) * W + px0 + bcol[b] + lc) * 3;
+                p[0] = out_accum ? ar[b] : -expm1f(-ar[b]);
+                p[1] = out_accum ? ag[b] : -expm1f(-ag[b]);
+                p[2] = out_accum ? ab[b] : -expm1f(-ab[b]);
             }
         } else {
             float *scr = fr.scratch + (int64_t)slot * 3 * T * T;
-            for (int k = tid; k < 3 * T * T; k += kSplatThreads) {
-                const int ch = k / (T * T), rem = k - ch * T * T;
-                const int r = rem / T, col = rem - r * T;
-                const float a = s_acc[ch * plane + r * stride + col];
-                if (a != 0.0f) atomicAdd(&scr[k], a);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (!((pvalid >> b) & 1u)) continue;
+                const int pix = (brow[b] + lr) * T + bcol[b] + lc;
+                if (ar[b] != 0.0f) atomicAdd(&scr[pix], ar[b]);
+                if (ag[b] != 0.0f) atomicAdd(&scr[T * T + pix], ag[b]);
+                if (ab[b] != 0.0f) atomicAdd(&scr[2 * T * T + pix], ab[b]);
             }
             __threadfence();
             __syncthreads();
@@ -342,6 +258,7 @@ __global__ void __launch_bounds__(kSplatThreads, 2) k_splat(SceneDev sc, FrameDe
             __syncthreads();
             if (s_last) {
                 __threadfence();
+                const int rowlen = 3 * tw;
                 for (int k = tid; k < th * rowlen; k += kSplatThreads) {
                     const int r = k / rowlen, cc = k - r * rowlen;
                     const int col = cc / 3, ch = cc - col * 3;
@@ -360,11 +277,11 @@ __global__ void __launch_bounds__(kSplatThreads, 2) k_splat(SceneDev sc, FrameDe
 typedef void (*SplatFn)(SceneDev, FrameDev, int *, float *, int);
 
 static SplatFn splat_fn(int T) {
-    const int nbw = blocks_per_warp(T);
-    if (nbw <= 1) return k_splat<1>;
-    if (nbw <= 2) return k_splat<2>;
-    if (nbw <= 4) return k_splat<4>;
-    if (nbw <= 8) return k_splat<8>;
+    const int nb = blocks_per_warp(T);
+    if (nb <= 1) return k_splat<1>;
+    if (nb <= 2) return k_splat<2>;
+    if (nb <= 4) return k_splat<4>;
+    if (nb <= 8) return k_splat<8>;
     return k_splat<16>;
 }
 
