@@ -246,6 +246,25 @@ splotch_status splotch_selftest_bounded_wait(int64_t limit_cycles, void *stream)
  * INVALID_ARG if no timed render has run on this thread. */
 splotch_status splotch_last_timing(double ms[4], int64_t counts[3]);
 
+/* Render one view without allocating any device memory.  The paper has no counterpart:
+ * this serves callers that cannot allocate while they render (a host application that
+ * owns all device memory, a real-time loop that forbids allocation after start-up, code
+ * enqueued inside a stream capture).  The frame workspace lives in a fixed 32 MiB device
+ * array inside this library, present on every GPU that loads the library until the
+ * process exits.  The caller passes the scene (created earlier with splotch_create_scene),
+ * the camera, the parameters and `out` (device, H x W x 3 FP32), as for splotch_render.
+ * The first call on a device looks up that device's copy of the array; make it before any
+ * stream capture.  The call waits for the frame (it synchronises `stream`).  All calls on
+ * a device share the array, so calls that overlap on the GPU (other threads, other
+ * streams) race and must be serialised by the caller.
+ * Limits: up to 2 MiB of per-chunk tile bases, 256 tiles split across work items, and the
+ * particle-tile records of the frame in the rest of the 32 MiB (16 bytes each; about 1.9
+ * million at 1024 tiles).  Frames beyond that return SPLOTCH_ERR_CAPACITY (the kernels skip
+ * the work; `out` is not written); images whose tile tables do not fit return
+ * SPLOTCH_ERR_UNSUPPORTED before any GPU work.  Other errors as splotch_render. */
+splotch_status splotch_render_noalloc(splotch_scene *scene, const splotch_camera *cam,
+                                      const splotch_render_params *params, float *out, void *stream);
+
 /* Static strings. */
 const char *splotch_status_string(splotch_status status);
 const char *splotch_last_error(void);

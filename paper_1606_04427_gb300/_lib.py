@@ -79,6 +79,8 @@ SIGNATURES = {
     "splotch_selftest_bounded_wait": ([C.c_int64, C.c_void_p], C.c_int),
     "splotch_final_transform": ([C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "splotch_last_timing": ([C.c_void_p, C.c_void_p], C.c_int),
+    "splotch_render_noalloc": ([C.c_void_p, C.POINTER(CameraC), C.POINTER(RenderParamsC), C.c_void_p,
+                                C.c_void_p], C.c_int),
     "splotch_status_string": ([C.c_int], C.c_char_p),
     "splotch_last_error": ([], C.c_char_p),
 }

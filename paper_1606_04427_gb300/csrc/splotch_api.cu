@@ -18,15 +18,13 @@ using namespace spl;
 // -----------------------------------------------------------------------------------------
 // errors
 
-static thread_local std::string g_err;
+static thread_local char g_err[512];
 
 static splotch_status fail(splotch_status s, const char *fmt, ...) {
-    char buf[512];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
-    g_err = buf;
     return s;
 }
 
@@ -51,7 +49,7 @@ extern "C" const char *splotch_status_string(splotch_status s) {
     return "unknown status";
 }
 
-extern "C" const char *splotch_last_error(void) { return g_err.c_str(); }
+extern "C" const char *splotch_last_error(void) { return g_err; }
 
 // -----------------------------------------------------------------------------------------
 // device memory: caller callbacks, or one stream-ordered pool per device
@@ -542,7 +540,7 @@ struct FrameHost {
 static const int64_t kRelBudget = 256ll << 20;
 
 static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_tiles, int T,
-                         int block_particles = 0) {
+                         int block_particles = 0, int64_t rel_budget = kRelBudget) {
     fh.V = V;
     fh.T = T;
     fh.n_tiles = n_tiles;
@@ -555,7 +553,7 @@ static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_ti
     const int groups = (V + fh.G - 1) / fh.G;
     int64_t target = std::max<int64_t>(1, (4 * n_sm + groups - 1) / groups);
     target = std::min(target, n_units);
-    const int64_t max_chunks = std::max<int64_t>(1, kRelBudget / (4ll * V * n_tiles));
+    const int64_t max_chunks = std::max<int64_t>(1, rel_budget / (4ll * V * n_tiles));
     int64_t nch = std::min(target, max_chunks);
     if (block_particles > 0) nch = std::min(max_chunks, std::max<int64_t>(1, (sc->n + block_particles - 1) / block_particles));
     const int64_t upc = (n_units + nch - 1) / nch;
@@ -1023,5 +1021,102 @@ extern "C" splotch_status splotch_selftest_bounded_wait(int64_t limit_cycles, vo
 extern "C" splotch_status splotch_final_transform(float *a, int64_t count, void *stream) {
     if (count < 0 || (count > 0 && !a)) return fail(SPLOTCH_ERR_INVALID_ARG, "bad buffer");
     CUDA_TRY(launch_final(a, count, (cudaStream_t)stream));
+    return SPLOTCH_OK;
+}
+
+// -----------------------------------------------------------------------------------------
+// Render without allocation.  Some callers cannot allocate device memory while rendering:
+// a host application that has reserved the whole GPU for its own memory manager, a
+// real-time loop whose rules forbid allocation after start-up, or code enqueued inside a
+// stream capture, where cudaMalloc is not allowed and allocation would synchronise the
+// device.  This path keeps the whole frame workspace in one fixed device array declared
+// below.  The CUDA runtime places that array on every GPU that loads this library, and it
+// stays there until the process exits.
+
+static constexpr size_t kStaticBytes = size_t(32) << 20;          // 32 MiB per GPU
+static constexpr int64_t kStaticRelBudget = int64_t(2) << 20;      // chunk bases: 2 MiB of it
+static constexpr int kStaticSplits = 256;                          // split-tile scratch slots
+static constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
+
+static std::mutex g_static_mu;
+static void *g_static_addr[kMaxDevices];  // device address of g_static_ws, per device
+
+// Device address of the fixed workspace on the current device.  Host code cannot use the
+// symbol's own name as a device pointer, so it asks the runtime once per device, with that
+// device current; later calls reuse the address.
+static splotch_status static_workspace(int dev, char **out) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(SPLOTCH_ERR_UNSUPPORTED, "device %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
+        if (e != cudaSuccess || !p)
+            return fail(SPLOTCH_ERR_CUDA, "cudaGetSymbolAddress of the fixed workspace: %s", cudaGetErrorString(e));
+        g_static_addr[dev] = p;
+    }
+    *out = static_cast<char *>(g_static_addr[dev]);
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_render_noalloc(splotch_scene *sc, const splotch_camera *cam,
+                                                 const splotch_render_params *params, float *out, void *stream) {
+    if (!sc || !cam || !out) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    splotch_render_params pr = params ? *params : splotch_default_params();
+    splotch_status s = check_params(&pr);
+    if (s != SPLOTCH_OK) return s;
+    if (cam->width < 1 || cam->height < 1) return fail(SPLOTCH_ERR_INVALID_ARG, "image size < 1");
+    if ((int64_t)cam->width * cam->height > (int64_t)1 << 30) return fail(SPLOTCH_ERR_UNSUPPORTED, "image larger than 2^30 px");
+    int T = 0;
+    s = choose_tile(cam->width, cam->height, pr.tile, &T);
+    if (s != SPLOTCH_OK) return s;
+    ViewParams vp;
+    s = make_view(cam, pr, T, vp);
+    if (s != SPLOTCH_OK) return s;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    char *base = nullptr;
+    s = static_workspace(dev, &base);
+    if (s != SPLOTCH_OK) return s;
+
+    // carve the fixed array: per-tile tables, then tile lists and split-tile scratch
+    FrameHost fh;
+    layout_fixed(fh, sc, 1, vp.n_tiles, T, pr.block_particles, kStaticRelBudget);
+    const size_t fixed = align256(fh.fixed_bytes);
+    const int splits = std::min(vp.n_tiles, kStaticSplits);
+    const size_t scratch = align256(sizeof(float) * 3 * (size_t)T * T * splits) + align256(sizeof(int) * splits);
+    if (fixed + scratch + 4096 > kStaticBytes)
+        return fail(SPLOTCH_ERR_UNSUPPORTED, "%d tiles of %d px need %zu bytes of tables, more than the %zu-byte fixed workspace",
+                    vp.n_tiles, T, fixed + scratch, kStaticBytes);
+    const int64_t pairs = (int64_t)((kStaticBytes - fixed - scratch - 1024) / sizeof(float4));
+    layout_var(fh, pairs, INT32_MAX, splits, false);
+    if (fixed + fh.var_bytes > kStaticBytes)
+        return fail(SPLOTCH_ERR_UNSUPPORTED, "fixed workspace layout overflow");
+    char *var = base + fixed;
+    FrameDev fr = frame_dev(fh, base, var);
+
+    // every call shares the array: zero what the kernels count into before they start
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(base + fh.o_views, &vp, sizeof(ViewParams), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(base + fh.o_counts, 0, sizeof(int) * (size_t)vp.n_tiles, st));
+    CUDA_TRY(cudaMemsetAsync(base + fh.o_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(cudaMemsetAsync(base + fh.o_queue, 0, sizeof(int) * 4, st));
+    CUDA_TRY(cudaMemsetAsync(var + fh.o_scratch, 0, fh.var_bytes - fh.o_scratch, st));
+    CUDA_TRY(launch_count(sc->storage, sc->dev_view, fr, st));
+    CUDA_TRY(launch_scan(fr, target_items(sc->dev, T), kMinItemPairs, st));
+    CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, st));
+    CUDA_TRY(launch_splat(sc->dev_view, fr, (int *)(base + fh.o_queue), out,
+                          (pr.flags & SPLOTCH_OUT_ACCUM) ? 1 : 0, sm_count(dev) * std::max(1, splat_blocks_per_sm(T)), st));
+    int64_t sizes[8];
+    int stat[4];
+    CUDA_TRY(cudaMemcpyAsync(sizes, base + fh.o_sizes, sizeof(sizes), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(stat, base + fh.o_status, sizeof(stat), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (stat[kStatTimeout]) return fail(SPLOTCH_ERR_TIMEOUT, "splat stage wait timed out");
+    if (stat[kStatOverflow])
+        return fail(SPLOTCH_ERR_CAPACITY,
+                    "frame needs %lld particle-tile pairs and %lld split tiles; the fixed %zu-byte workspace holds %lld and %d",
+                    (long long)sizes[kSizePairs], (long long)sizes[kSizeSplits], kStaticBytes, (long long)pairs, splits);
     return SPLOTCH_OK;
 }

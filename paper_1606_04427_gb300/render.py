@@ -163,6 +163,21 @@ class Scene:
                                        _stream_handle(stream)), "render")
         return out[0] if single and out.dim() == 4 else out
 
+    def render_noalloc(self, cam, out: torch.Tensor, params: Optional[RenderParams] = None,
+                       stream=None) -> torch.Tensor:
+        """Render one camera into ``out`` (H x W x 3 FP32, on the device) without any
+        device allocation: the library's fixed 32 MiB workspace holds the frame.  For
+        callers that may not allocate while they render.  Blocks until the frame is done.
+        Calls that overlap on the GPU share that workspace and must not run at once."""
+        H, W = int(cam.height), int(cam.width)
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        assert out.numel() == H * W * 3
+        p = (params or RenderParams()).c()
+        c = _lib.camera_c(cam)
+        check(self._lib.splotch_render_noalloc(self.handle, C.byref(c), C.byref(p), out.data_ptr(),
+                                               _stream_handle(stream)), "render_noalloc")
+        return out
+
     def debug_raster(self, cam, params: Optional[RenderParams] = None, stream=None):
         out = torch.empty((8, max(1, self.n)), dtype=torch.float32, device="cuda")
         p = (params or RenderParams()).c()
