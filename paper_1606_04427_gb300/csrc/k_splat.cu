@@ -42,17 +42,21 @@ __device__ __forceinline__ int find_tile(const int *__restrict__ item_off, int N
     return a;
 }
 
-// blocks of 8 x 4 pixels; warp w owns block rows w, w + 8, ...; NB blocks per warp
-__host__ __device__ __forceinline__ int blocks_per_warp(int T) {
-    const int bxn = (T + 7) >> 3, byn = (T + 3) >> 2;
-    return bxn * ((byn + kSplatWarps - 1) / kSplatWarps);
+// blocks of 8 x 4 pixels; warp w owns block rows w, w + 8, ...: NR block rows of NC
+// blocks each (NC = ceil(T / 8), NR = ceil(ceil(T / 4) / 8))
+__host__ __device__ __forceinline__ int block_cols(int T) { return (T + 7) >> 3; }
+__host__ __device__ __forceinline__ int block_rows_per_warp(int T) {
+    return (((T + 3) >> 2) + kSplatWarps - 1) / kSplatWarps;
 }
 
 size_t splat_smem_bytes(int) {
     return sizeof(float4) * 2 * kStage + sizeof(Rec) * kStage + sizeof(short) * kSplatWarps * kStage;
 }
 
-template <int NB>
+// pixel centre coordinate that no support reaches (its square overflows to +inf)
+constexpr float kFar = 1e30f;
+
+template <int NR, int NC>
 __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDev fr, int *queue, float *out,
                                                          int out_accum) {
     if (fr.status[kStatOverflow]) return;
@@ -72,18 +76,7 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
     const int64_t K = fr.sizes[kSizeK];
     const ViewParams g0 = fr.views[0];
     const int T = g0.T, W = g0.W, H = g0.H, ntx = g0.ntx;
-    const int bxn = (T + 7) >> 3, byn = (T + 3) >> 2;
     const int lc = lane & 7, lr = lane >> 3;
-
-    // this warp's blocks: tile-local origins (empty blocks get an origin beyond the tile)
-    int bcol[NB], brow[NB];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const int br = warp + kSplatWarps * (b / bxn), bc = b % bxn;
-        const bool ok = b < bxn * ((byn + kSplatWarps - 1) / kSplatWarps) && br < byn;
-        bcol[b] = ok ? bc * 8 : 1 << 20;
-        brow[b] = ok ? br * 4 : 1 << 20;
-    }
 
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
@@ -114,15 +107,17 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
         const int nrec = (int)(min(seg1, e0 + K) - e0);
         const int nst = (nrec + kStage - 1) / kStage;
 
-        // this lane's pixel in each block: centre coordinates and accumulators
-        float fx[NB], fy[NB], ar[NB], ag[NB], ab[NB];
-        unsigned pvalid = 0;
+        // this lane's pixels: column c * 8 + lc of block row warp + 8 rr (tile rows
+        // 4 (warp + 8 rr) + lr); pixels outside the tile get a centre no support reaches
+        float fx[NC], fy[NR], ar[NR][NC], ag[NR][NC], ab[NR][NC];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            fx[b] = (float)(px0 + bcol[b] + lc) + 0.5f;
-            fy[b] = (float)(py0 + brow[b] + lr) + 0.5f;
-            ar[b] = ag[b] = ab[b] = 0.0f;
-            if (bcol[b] + lc < tw && brow[b] + lr < th) pvalid |= 1u << b;
+        for (int c = 0; c < NC; ++c) fx[c] = c * 8 + lc < tw ? (float)(px0 + c * 8 + lc) + 0.5f : kFar;
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+            const int row = 4 * (warp + kSplatWarps * rr) + lr;
+            fy[rr] = row < th ? (float)(py0 + row) + 0.5f : kFar;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ar[rr][c] = ag[rr][c] = ab[rr][c] = 0.0f;
         }
 
         if (tid == 0 && nrec > 0) {
@@ -197,7 +192,6 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
             __syncthreads();
 
             // ---- 2. gather: this warp's list over this warp's blocks ---------------------
-            // blocks b = rr * bxn + bc: block row rr of this warp (tile rows brow), column bc
             const int nmine = s_wcnt[warp];
             const short *mine = s_wl + warp * kStage;
             for (int k = 0; k < nmine; ++k) {
@@ -205,25 +199,25 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 const int4 box = *reinterpret_cast<const int4 *>(&q->ilo);
                 const float4 pa = *reinterpret_cast<const float4 *>(&q->X);
                 const float4 pb = *reinterpret_cast<const float4 *>(&q->er);
-                const int bc_lo = box.x >> 3, bc_hi = box.y >> 3;  // overlapped block columns
-                // rows of this warp's blocks repeat every bxn blocks: one dy^2 per block row
-                float dy2[NB];
+                // block columns the box overlaps, as a bit mask (uniform over the warp)
+                const uint32_t cm = (2u << (box.y >> 3)) - (1u << (box.x >> 3));
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const float dy = __fsub_rn(fy[b], pa.y);
-                    dy2[b] = __fmul_rn(dy, dy);
-                }
+                for (int rr = 0; rr < NR; ++rr) {
+                    const int r0 = 4 * (warp + kSplatWarps * rr);
+                    if (NR > 1 && (r0 > box.w || r0 + 3 < box.z)) continue;
+                    const float dy = __fsub_rn(fy[rr], pa.y);
+                    const float dy2 = __fmul_rn(dy, dy);
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const int bc = bcol[b] >> 3;
-                    if (bc < bc_lo || bc > bc_hi || brow[b] > box.w || brow[b] + 3 < box.z) continue;
-                    const float dx = __fsub_rn(fx[b], pa.x);
-                    const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2[b]);
-                    if (((pvalid >> b) & 1u) && d2 < pa.z) {
-                        const float w = ex2_fast(d2 * pa.w);
-                        ar[b] += pb.x * w;
-                        ag[b] += pb.y * w;
-                        ab[b] += pb.z * w;
+                    for (int c = 0; c < NC; ++c) {
+                        if (!(cm & (1u << c))) continue;
+                        const float dx = __fsub_rn(fx[c], pa.x);
+                        const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2);
+                        if (d2 < pa.z) {
+                            const float w = ex2_fast(d2 * pa.w);
+                            ar[rr][c] += pb.x * w;
+                            ag[rr][c] += pb.y * w;
+                            ab[rr][c] += pb.z * w;
+                        }
                     }
                 }
             }
@@ -235,22 +229,32 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
         float *o = out + (int64_t)v * H * W * 3;
         if (slot < 0) {
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                if (!((pvalid >> b) & 1u)) continue;
-                float *p = o + ((int64_t)(py0 + brow[b] + lr) * W + px0 + bcol[b] + lc) * 3;
-                p[0] = out_accum ? ar[b] : -expm1f(-ar[b]);
-                p[1] = out_accum ? ag[b] : -expm1f(-ag[b]);
-                p[2] = out_accum ? ab[b] : -expm1f(-ab[b]);
+            for (int rr = 0; rr < NR; ++rr) {
+                const int row = 4 * (warp + kSplatWarps * rr) + lr;
+                if (row >= th) continue;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c * 8 + lc >= tw) continue;
+                    float *p = o + ((int64_t)(py0 + row) * W + px0 + c * 8 + lc) * 3;
+                    p[0] = out_accum ? ar[rr][c] : -expm1f(-ar[rr][c]);
+                    p[1] = out_accum ? ag[rr][c] : -expm1f(-ag[rr][c]);
+                    p[2] = out_accum ? ab[rr][c] : -expm1f(-ab[rr][c]);
+                }
             }
         } else {
             float *scr = fr.scratch + (int64_t)slot * 3 * T * T;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                if (!((pvalid >> b) & 1u)) continue;
-                const int pix = (brow[b] + lr) * T + bcol[b] + lc;
-                if (ar[b] != 0.0f) atomicAdd(&scr[pix], ar[b]);
-                if (ag[b] != 0.0f) atomicAdd(&scr[T * T + pix], ag[b]);
-                if (ab[b] != 0.0f) atomicAdd(&scr[2 * T * T + pix], ab[b]);
+            for (int rr = 0; rr < NR; ++rr) {
+                const int row = 4 * (warp + kSplatWarps * rr) + lr;
+                if (row >= th) continue;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c * 8 + lc >= tw) continue;
+                    const int pix = row * T + c * 8 + lc;
+                    if (ar[rr][c] != 0.0f) atomicAdd(&scr[pix], ar[rr][c]);
+                    if (ag[rr][c] != 0.0f) atomicAdd(&scr[T * T + pix], ag[rr][c]);
+                    if (ab[rr][c] != 0.0f) atomicAdd(&scr[2 * T * T + pix], ab[rr][c]);
+                }
             }
             __threadfence();
             __syncthreads();
@@ -277,12 +281,21 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
 typedef void (*SplatFn)(SceneDev, FrameDev, int *, float *, int);
 
 static SplatFn splat_fn(int T) {
-    const int nb = blocks_per_warp(T);
-    if (nb <= 1) return k_splat<1>;
-    if (nb <= 2) return k_splat<2>;
-    if (nb <= 4) return k_splat<4>;
-    if (nb <= 8) return k_splat<8>;
-    return k_splat<16>;
+    const int nc = block_cols(T);
+    if (block_rows_per_warp(T) <= 1) {
+        switch (nc) {
+            case 1: return k_splat<1, 1>;
+            case 2: return k_splat<1, 2>;
+            case 3: return k_splat<1, 3>;
+            default: return k_splat<1, 4>;
+        }
+    }
+    switch (nc) {
+        case 5: return k_splat<2, 5>;
+        case 6: return k_splat<2, 6>;
+        case 7: return k_splat<2, 7>;
+        default: return k_splat<2, 8>;
+    }
 }
 
 int splat_blocks_per_sm(int T) {
