@@ -68,6 +68,8 @@ def _bind(path: str):
     lib.orc_bin.argtypes = scene + [i32, P, P, P, i64, P]
     lib.orc_covered_pixels.argtypes = scene + [i64, P, i64]
     lib.orc_covered_pixels.restype = i64
+    lib.orc_count_work.argtypes = scene + [i32, P]
+    lib.orc_count_work.restype = i32
     lib.orc_final.argtypes = [i64, P, P]
     lib.orc_num_threads.restype = i32
     lib.orc_set_threads.argtypes = [i32]
@@ -289,6 +291,16 @@ def bins(ps, cam, params: Params = Params(), storage: str = "f32"):
     rc = lib.orc_bin(*s.args(), T, _ptr(counts), _ptr(offs), _ptr(mem), mem.shape[0], _ptr(total))
     assert rc == 0
     return counts, offs, mem[: int(total[0])]
+
+
+def count_work(ps, cam, params: Params = Params(), storage: str = "f32", tile: int = 0) -> dict:
+    """Active particles, covered (particle, pixel) pairs and, for tile > 0, (particle,
+    tile) pairs of one frame."""
+    s = _Scene(ps, cam, params, storage)
+    out = np.zeros(3, np.int64)
+    rc = _cur().orc_count_work(*s.args(), int(tile), _ptr(out))
+    assert rc == 0, rc
+    return {"active": int(out[0]), "pixel_pairs": int(out[1]), "tile_pairs": int(out[2])}
 
 
 def covered_pixels(ps, cam, k: int, params: Params = Params(), storage: str = "f32") -> np.ndarray:

@@ -541,6 +541,36 @@ int orc_bin(SCENE_ARGS, int T, int32_t *counts, int64_t *offsets, int32_t *membe
     return ORC_OK;
 }
 
+/* Work of one frame, in the units the splat and binning costs are counted in:
+ * out[0] = active particles, out[1] = covered (particle, pixel) pairs, i.e. kernel
+ * evaluations the definition of Section 2.1 makes (every pixel whose centre lies inside a
+ * particle's support gets one), out[2] = (particle, tile) pairs under the tile rule of
+ * Section 3.2.1 with edge T (0 skips it). */
+int orc_count_work(SCENE_ARGS, int T, int64_t *out)
+{
+    orc_scene s;
+    fill_scene(&s, SCENE_PASS);
+    orc_px *px = raster_all(&s, NULL);
+    if (!px) return 2;
+    int64_t act = 0, cov = 0, tp = 0;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(+ : act, cov, tp)
+    for (int64_t k = 0; k < n; ++k) {
+        const orc_px *o = &px[k];
+        if (!o->active) continue;
+        ++act;
+        for (int j = o->j0; j <= o->j1; ++j)
+            for (int i = o->i0; i <= o->i1; ++i) cov += covered(o, i, j);
+        if (T > 0)
+            for (int ty = o->j0 / T; ty <= o->j1 / T; ++ty)
+                for (int tx = o->i0 / T; tx <= o->i1 / T; ++tx) tp += tile_member(o, tx, ty, T);
+    }
+    out[0] = act;
+    out[1] = cov;
+    out[2] = tp;
+    free(px);
+    return ORC_OK;
+}
+
 /* Tiled render (Section 3.1: each tile renders its own particle list, pixels stay local to
  * the tile): for every tile, its members in list order, the covered pixels of the tile. */
 int orc_render_tiled(SCENE_ARGS, int T, double *a)

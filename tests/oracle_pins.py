@@ -249,6 +249,43 @@ def pin_binning_conservative():
                 assert k in lists[(j // T) * ntx + (i // T)], (T, k, i, j)
 
 
+def pin_work_counts():
+    """The frame's work units: covered (particle, pixel) pairs equal, for one particle
+    centred on a lattice corner, the half-integer lattice points strictly inside its
+    support disc, and for a random scene the pairs a per-pixel FP32 brute force finds;
+    (particle, tile) pairs equal the binning's total."""
+    W = H = 96
+    for R_px in (0.75, 3.0, 7.25, 20.0):
+        ps, cam = _single(R_px, W, H, X=48.0, Y=40.0)
+        r = oracle.raster(ps, cam)
+        X, Y, R = r["X"][0], r["Y"][0], r["R"][0]
+        assert abs(X - 48.0) < 1e-3 and abs(Y - 40.0) < 1e-3
+        k = np.arange(-64, 64) + 0.5
+        lattice = int(((k[:, None] ** 2 + k[None, :] ** 2) < R * R).sum())
+        w = oracle.count_work(ps, cam)
+        assert w["active"] == 1 and w["pixel_pairs"] == lattice, (R_px, w, lattice)
+    rng = np.random.default_rng(9)
+    n = 300
+    ps = make_set(rng.uniform(-0.1, 1.1, n), rng.uniform(-0.1, 1.1, n), rng.uniform(0, 1.2, n),
+                  np.exp(rng.uniform(np.log(0.002), np.log(0.06), n)))
+    cam = front(70, 50)
+    r = oracle.raster(ps, cam)
+    f = np.float32
+    ii = np.arange(70, dtype=f) + f(0.5)
+    jj = np.arange(50, dtype=f) + f(0.5)
+    want = 0
+    for q in np.nonzero(r["active"])[0]:
+        X, Y, R = f(r["X"][q]), f(r["Y"][q]), f(r["R"][q])
+        dx = ii[None, :] - X
+        dy = jj[:, None] - Y
+        want += int(((dx * dx + dy * dy) < R * R).sum())
+    for T in (8, 16, 32):
+        w = oracle.count_work(ps, cam, tile=T)
+        assert w["active"] == int(r["active"].sum()) and w["pixel_pairs"] == want, (T, w, want)
+        counts, _, _ = oracle.bins(ps, cam, oracle.Params(tile=T))
+        assert w["tile_pairs"] == int(counts.sum()), (T, w)
+
+
 def pin_tile_threshold():
     """Membership flips where the distance to the tile centre crosses support +
     half the tile diagonal (sqrt(2) T / 2)."""
