@@ -115,7 +115,8 @@ typedef struct {
 
 /* Render parameters.
  *   tile          square tile edge in pixels, 1..64, with at most 16384 tiles per image;
- *                 0 = 32 (or the smallest edge above 32 that meets the tile limit).
+ *                 0 = 16 (or the smallest edge above 16, in steps of 8, that meets
+ *                 the tile limit).
  *                 Section 3.1: the tile size is a runtime parameter.
  *   rfac          support radius factor, > 0 (0.75; Section 3.2.1 threshold)
  *   sigma_over_R  Gaussian sigma as a fraction of the support, > 0 (0.5)

@@ -133,16 +133,32 @@ __global__ void __launch_bounds__(kThreads) k_count(SceneDev sc, FrameDev fr) {
 
     const int64_t s = (int64_t)b * fr.chunk;
     const int64_t e = min(sc.n, s + fr.chunk);
-    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
-        const float x = load1<S>(sc.x, i), y = load1<S>(sc.y, i), z = load1<S>(sc.z, i), h = load1<S>(sc.h, i);
+    // the next particle's attributes are loaded before this one is binned, so a load is
+    // always in flight behind the shared-memory work.  The loop runs warp-uniformly (a
+    // lane past the chunk end idles) so that particles whose candidate box is larger than
+    // 2 x 2 tiles can be binned by the whole warp, one such particle at a time.
+    const int lane = threadIdx.x & 31;
+    int64_t i = s + threadIdx.x;
+    float nx = 0.0f, ny = 0.0f, nz = 0.0f, nh = 0.0f;
+    if (i < e) nx = load1<S>(sc.x, i), ny = load1<S>(sc.y, i), nz = load1<S>(sc.z, i), nh = load1<S>(sc.h, i);
+    for (; i - lane < e; i += blockDim.x) {
+        const bool valid = i < e;
+        const float x = nx, y = ny, z = nz, h = nh;
+        const int64_t inext = i + blockDim.x;
+        if (inext < e)
+            nx = load1<S>(sc.x, inext), ny = load1<S>(sc.y, inext), nz = load1<S>(sc.z, inext),
+            nh = load1<S>(sc.h, inext);
         for (int g = 0; g < g_n; ++g) {
             const ViewParams &vp = s_view[g];
-            Raster r;
-            if (!raster_one(vp, x, y, z, h, r)) continue;
             int *hist = s_hist + g * nt;
-            const int tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
-            const int ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
-            if (tx1 - tx0 <= 1 && ty1 - ty0 <= 1) {
+            Raster r;
+            int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+            if (valid && raster_one(vp, x, y, z, h, r)) {
+                tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
+                ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
+            }
+            const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
+            if (small) {
                 // at most 2 x 2 candidate tiles: the common case, tested without loops
                 const bool m00 = tile_member(vp, r.X, r.Y, r.R, tx0, ty0);
                 const bool m10 = tx1 > tx0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty0);
@@ -153,10 +169,20 @@ __global__ void __launch_bounds__(kThreads) k_count(SceneDev sc, FrameDev fr) {
                 if (m10) atomicAdd(&hist[t00 + 1], 1);
                 if (m01) atomicAdd(&hist[t00 + vp.ntx], 1);
                 if (m11) atomicAdd(&hist[t00 + vp.ntx + 1], 1);
-            } else {
-                for (int ty = ty0; ty <= ty1; ++ty)
-                    for (int tx = tx0; tx <= tx1; ++tx)
-                        if (tile_member(vp, r.X, r.Y, r.R, tx, ty)) atomicAdd(&hist[ty * vp.ntx + tx], 1);
+            }
+            uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
+            while (big) {
+                const int src = __ffs(big) - 1;
+                big &= big - 1;
+                const float bX = __shfl_sync(0xffffffffu, r.X, src), bY = __shfl_sync(0xffffffffu, r.Y, src);
+                const float bR = __shfl_sync(0xffffffffu, r.R, src);
+                const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
+                const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
+                const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
+                for (int k = lane; k < ncand; k += 32) {
+                    const int ty = by0 + k / bw, tx = bx0 + k % bw;
+                    if (tile_member(vp, bX, bY, bR, tx, ty)) atomicAdd(&hist[ty * vp.ntx + tx], 1);
+                }
             }
         }
     }
@@ -294,6 +320,13 @@ __global__ void __launch_bounds__(1024) k_scan(FrameDev fr, int target_items, in
         run_i += ti;
         run_s += ts;
     }
+    __syncthreads();
+    // per-view segment sizes must fit the scatter's 32-bit cursors
+    int big = 0;
+    for (int v = threadIdx.x; v < fr.V; v += blockDim.x)
+        big |= (fr.offsets[(int64_t)v * fr.n_tiles + fr.n_tiles - 1] + fr.counts[(int64_t)v * fr.n_tiles + fr.n_tiles - 1] -
+                fr.offsets[(int64_t)v * fr.n_tiles]) > (long long)INT32_MAX;
+    big = __syncthreads_or(big);
     if (threadIdx.x == 0) {
         fr.offsets[N] = run_p;
         fr.item_off[N] = run_i;
@@ -302,7 +335,7 @@ __global__ void __launch_bounds__(1024) k_scan(FrameDev fr, int target_items, in
         fr.sizes[kSizeSplits] = run_s;
         fr.sizes[kSizeK] = K;
         fr.sizes[kSizeMaxCount] = mx_all;
-        const bool over = run_p > fr.pair_cap || run_i > fr.item_cap || run_s > fr.split_cap;
+        const bool over = run_p > fr.pair_cap || run_i > fr.item_cap || run_s > fr.split_cap || big;
         fr.status[kStatOverflow] = over ? 1 : 0;
     }
 }
@@ -319,8 +352,11 @@ cudaError_t launch_scan(const FrameDev &fr, int target_items, int kmin, cudaStre
 template <int S>
 __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) {
     if (fr.status[kStatOverflow]) return;
+    // cursor of this chunk's slice of every tile segment, relative to the start of the
+    // view's segments (a view holds fewer than 2^31 pairs: the scan checks it)
     extern __shared__ int s_cur[];  // [g_n][n_tiles]
     __shared__ ViewParams s_view[kMaxGroup];
+    __shared__ int64_t s_vbase[kMaxGroup];
     __shared__ int64_t s_tb[kMaxTypes + 1];
     const int b = blockIdx.x;
     const int v0 = blockIdx.y * fr.G;
@@ -328,32 +364,51 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
     const int nt = fr.n_tiles;
     for (int k = threadIdx.x; k < g_n * nt; k += blockDim.x) {
         const int g = k / nt, t = k - g * nt;
-        s_cur[k] = fr.rel[((int64_t)(v0 + g) * fr.n_chunks + b) * nt + t];
+        const int64_t *seg = fr.offsets + (int64_t)(v0 + g) * nt;
+        s_cur[k] = (int)(seg[t] - seg[0]) + fr.rel[((int64_t)(v0 + g) * fr.n_chunks + b) * nt + t];
     }
-    if (threadIdx.x < g_n) s_view[threadIdx.x] = fr.views[v0 + threadIdx.x];
+    if (threadIdx.x < g_n) {
+        s_view[threadIdx.x] = fr.views[v0 + threadIdx.x];
+        s_vbase[threadIdx.x] = fr.offsets[(int64_t)(v0 + threadIdx.x) * nt];
+    }
     for (int k = threadIdx.x; k <= sc.n_types; k += blockDim.x) s_tb[k] = sc.type_begin[k];
     __syncthreads();
 
     const int64_t s = (int64_t)b * fr.chunk;
     const int64_t e = min(sc.n, s + fr.chunk);
     int type = 0;
-    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
-        const float x = load1<S>(sc.x, i), y = load1<S>(sc.y, i), z = load1<S>(sc.z, i), h = load1<S>(sc.h, i);
-        const float itn = load1<S>(sc.it, i);
-        while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
+    const int lane = threadIdx.x & 31;
+    int64_t i = s + threadIdx.x;
+    float nx = 0.0f, ny = 0.0f, nz = 0.0f, nh = 0.0f, ni = 0.0f;
+    if (i < e)
+        nx = load1<S>(sc.x, i), ny = load1<S>(sc.y, i), nz = load1<S>(sc.z, i), nh = load1<S>(sc.h, i),
+        ni = load1<S>(sc.it, i);
+    for (; i - lane < e; i += blockDim.x) {
+        const bool valid = i < e;
+        const float x = nx, y = ny, z = nz, h = nh, itn = ni;
+        const int64_t inext = i + blockDim.x;
+        if (inext < e)
+            nx = load1<S>(sc.x, inext), ny = load1<S>(sc.y, inext), nz = load1<S>(sc.z, inext),
+            nh = load1<S>(sc.h, inext), ni = load1<S>(sc.it, inext);
+        if (valid)
+            while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
         uint32_t q = __float2uint_rn(__fmul_rn(itn, (float)kCodeMax));
         q = min(q, kCodeMax);
         const float code = __uint_as_float(((uint32_t)type << 24) | q);
         for (int g = 0; g < g_n; ++g) {
             const ViewParams &vp = s_view[g];
-            Raster r;
-            if (!raster_one(vp, x, y, z, h, r)) continue;
             int *cur = s_cur + g * nt;
-            const int64_t *seg = fr.offsets + (int64_t)(v0 + g) * nt;
-            const float4 rec = make_float4(r.X, r.Y, r.R, code);
-            const int tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
-            const int ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
-            if (tx1 - tx0 <= 1 && ty1 - ty0 <= 1) {
+            float4 *lists = fr.lists + s_vbase[g];
+            int *pids = fr.pids ? fr.pids + s_vbase[g] : nullptr;
+            Raster r;
+            int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+            if (valid && raster_one(vp, x, y, z, h, r)) {
+                tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
+                ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
+            }
+            const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
+            if (small) {
+                const float4 rec = make_float4(r.X, r.Y, r.R, code);
                 const int t00 = ty0 * vp.ntx + tx0;
 #pragma unroll
                 for (int qd = 0; qd < 4; ++qd) {
@@ -361,19 +416,33 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
                     if ((dx && tx1 == tx0) || (dy && ty1 == ty0)) continue;
                     if (!tile_member(vp, r.X, r.Y, r.R, tx0 + dx, ty0 + dy)) continue;
                     const int t = t00 + dy * vp.ntx + dx;
-                    const int64_t pos = seg[t] + atomicAdd(&cur[t], 1);
-                    fr.lists[pos] = rec;
-                    if (fr.pids) fr.pids[pos] = (int)i;
+                    const int pos = atomicAdd(&cur[t], 1);
+                    lists[pos] = rec;
+                    if (pids) pids[pos] = (int)i;
                 }
-            } else {
-                for (int ty = ty0; ty <= ty1; ++ty)
-                    for (int tx = tx0; tx <= tx1; ++tx)
-                        if (tile_member(vp, r.X, r.Y, r.R, tx, ty)) {
-                            const int t = ty * vp.ntx + tx;
-                            const int64_t pos = seg[t] + atomicAdd(&cur[t], 1);
-                            fr.lists[pos] = rec;
-                            if (fr.pids) fr.pids[pos] = (int)i;
-                        }
+            }
+            // particles with more than 2 x 2 candidate tiles: the whole warp bins each one
+            uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
+            while (big) {
+                const int src = __ffs(big) - 1;
+                big &= big - 1;
+                const float bX = __shfl_sync(0xffffffffu, r.X, src), bY = __shfl_sync(0xffffffffu, r.Y, src);
+                const float bR = __shfl_sync(0xffffffffu, r.R, src);
+                const float bcode = __shfl_sync(0xffffffffu, code, src);
+                const int bid = __shfl_sync(0xffffffffu, (int)i, src);
+                const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
+                const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
+                const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
+                const float4 rec = make_float4(bX, bY, bR, bcode);
+                for (int k = lane; k < ncand; k += 32) {
+                    const int ty = by0 + k / bw, tx = bx0 + k % bw;
+                    if (tile_member(vp, bX, bY, bR, tx, ty)) {
+                        const int t = ty * vp.ntx + tx;
+                        const int pos = atomicAdd(&cur[t], 1);
+                        lists[pos] = rec;
+                        if (pids) pids[pos] = bid;
+                    }
+                }
             }
         }
     }
@@ -393,6 +462,26 @@ cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, 
     if (storage == 0) return scatter_impl<0>(sc, fr, st);
     if (storage == 1) return scatter_impl<1>(sc, fr, st);
     return scatter_impl<2>(sc, fr, st);
+}
+
+// Resident CTAs per SM of the binning kernels with a histogram of `smem` bytes (the
+// smaller of count and scatter, so both run their chunks in whole waves).
+template <int S> static int bin_occupancy(size_t smem) {
+    int a = 0, b = 0;
+    if (cudaFuncSetAttribute(k_count<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_scatter<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_count<S>, kThreads, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scatter<S>, kThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(1, std::min(a, b));
+}
+
+int bin_ctas_per_sm(int storage, size_t smem) {
+    if (storage == 0) return bin_occupancy<0>(smem);
+    if (storage == 1) return bin_occupancy<1>(smem);
+    return bin_occupancy<2>(smem);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -278,19 +278,335 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
     }
 }
 
-typedef void (*SplatFn)(SceneDev, FrameDev, int *, float *, int);
+// ---------------------------------------------------------------------------------------
+// Warp-per-item splat for tiles up to 24 px.  One warp owns every pixel of its item's tile
+// (NR x NC blocks of 8 x 4 pixels, all in registers), so the warps of a CTA never wait on
+// one another: in clustered data the density inside a tile is far from uniform, and with
+// the tile's pixel rows shared out among the CTA's warps the busiest warp set the pace.
+// Each warp stages its item's records by bulk copy into its own double buffer; each lane
+// decodes one record of a 32-record group (pixel box, block mask, colour, Gaussian
+// scale) into a small shared table, and the warp then walks the live records, evaluating
+// only the blocks the record's box overlaps.
 
-static SplatFn splat_fn(int T) {
-    const int nc = block_cols(T);
-    if (block_rows_per_warp(T) <= 1) {
-        switch (nc) {
-            case 1: return k_splat<1, 1>;
-            case 2: return k_splat<1, 2>;
-            case 3: return k_splat<1, 3>;
-            default: return k_splat<1, 4>;
+constexpr int kWarpsPerCta = 4;
+constexpr int kWStage = 128;  // records per bulk copy, per warp
+
+struct __align__(16) WRec {
+    float X, Y, R2, kr;
+    float er, eg, eb;
+    uint32_t mask;  // blocks (r * NC + c) the record's box overlaps
+};
+
+struct __align__(16) WarpSmem {
+    float4 buf[2][kWStage];
+    WRec dec[32];
+    uint64_t bar[2];
+    uint64_t pad;
+};
+
+template <int NR, int NC>
+struct WarpShape {
+    static constexpr int kBlocks = NR * NC;
+    static_assert(kBlocks <= 32, "block mask is 32 bits");
+    // a 1 at the first block of every block row: multiplying an NC-bit column mask by it
+    // repeats the mask in every row
+    static constexpr uint64_t kRowRep = []() {
+        uint64_t r = 0;
+        for (int i = 0; i < NR; ++i) r |= 1ull << (i * NC);
+        return r;
+    }();
+    // resident CTAs per SM, which caps the registers: below about 80 per thread the
+    // compiler reloads record fields from shared memory instead of keeping them
+    static constexpr int kMinCtas = kBlocks <= 2 ? 8 : (kBlocks <= 8 ? 6 : (kBlocks <= 18 ? 4 : 3));
+};
+
+// Index of the block range [a, b] among the n (n + 1) / 2 ranges of n blocks.
+__host__ __device__ constexpr int range_id(int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); }
+
+// Straight-line splat of one record over the block rectangle rows [R0, R1] x columns
+// [C0, C1]: every lane evaluates its pixel of each block, uncovered pixels add zero.
+template <int NR, int NC, int R0, int R1, int C0, int C1>
+__device__ __forceinline__ void rect_splat(const float (&fx)[NC], const float (&fy)[NR], float (&ar)[NR][NC],
+                                           float (&ag)[NR][NC], float (&ab)[NR][NC], const float4 &pa,
+                                           const float4 &pb) {
+#pragma unroll
+    for (int r = R0; r <= R1; ++r) {
+        const float dy = __fsub_rn(fy[r], pa.y);
+        const float dy2 = __fmul_rn(dy, dy);
+#pragma unroll
+        for (int c = C0; c <= C1; ++c) {
+            const float dx = __fsub_rn(fx[c], pa.x);
+            const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2);
+            float w = ex2_fast(d2 * pa.w);
+            w = d2 < pa.z ? w : 0.0f;
+            ar[r][c] += pb.x * w;
+            ag[r][c] += pb.y * w;
+            ab[r][c] += pb.z * w;
         }
     }
-    switch (nc) {
+}
+
+// One indirect jump per record to the code of its block rectangle (tiles of 8 x 8 and
+// 16 x 16 pixels: 3 and 30 rectangles).
+#define SPL_RECT(R0, R1, C0, C1)                                                              \
+    case range_id(R0, R1, NR) * (NC * (NC + 1) / 2) + range_id(C0, C1, NC):                  \
+        rect_splat<NR, NC, R0, R1, C0, C1>(fx, fy, ar, ag, ab, pa, pb);                       \
+        break;
+#define SPL_ROWS4(C0, C1)                                                                      \
+    SPL_RECT(0, 0, C0, C1) SPL_RECT(0, 1, C0, C1) SPL_RECT(0, 2, C0, C1) SPL_RECT(0, 3, C0, C1) \
+    SPL_RECT(1, 1, C0, C1) SPL_RECT(1, 2, C0, C1) SPL_RECT(1, 3, C0, C1) SPL_RECT(2, 2, C0, C1) \
+    SPL_RECT(2, 3, C0, C1) SPL_RECT(3, 3, C0, C1)
+
+template <int NR, int NC>
+__device__ __forceinline__ void rect_dispatch(int id, const float (&fx)[NC], const float (&fy)[NR],
+                                              float (&ar)[NR][NC], float (&ag)[NR][NC], float (&ab)[NR][NC],
+                                              const float4 &pa, const float4 &pb) {
+    if constexpr (NR == 2 && NC == 1) {
+        switch (id) {
+            SPL_RECT(0, 0, 0, 0)
+            SPL_RECT(0, 1, 0, 0)
+            SPL_RECT(1, 1, 0, 0)
+            default: break;
+        }
+    } else if constexpr (NR == 4 && NC == 2) {
+        switch (id) {
+            SPL_ROWS4(0, 0)
+            SPL_ROWS4(0, 1)
+            SPL_ROWS4(1, 1)
+            default: break;
+        }
+    }
+}
+#undef SPL_ROWS4
+#undef SPL_RECT
+
+template <int NR, int NC>
+constexpr bool kRectDispatch = (NR == 2 && NC == 1) || (NR == 4 && NC == 2);
+
+template <int NR, int NC>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCtas))
+    k_splat_warp(SceneDev sc, FrameDev fr, int *queue, float *out, int out_accum) {
+    using Shape = WarpShape<NR, NC>;
+    if (fr.status[kStatOverflow]) return;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_raw) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int nt = fr.n_tiles;
+    const int N = fr.V * nt;
+    const int total_items = (int)fr.sizes[kSizeItems];
+    const int64_t K = fr.sizes[kSizeK];
+    const ViewParams g0 = fr.views[0];
+    const int T = g0.T, W = g0.W, H = g0.H, ntx = g0.ntx;
+    const int lc = lane & 7, lr = lane >> 3;
+
+    if (lane == 0) {
+        mbar_init(&ws->bar[0], 1);
+        mbar_init(&ws->bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    uint32_t phase0 = 0, phase1 = 0;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(queue, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total_items) break;
+
+        const int gt = find_tile(fr.item_off, N, item);
+        const int v = gt / nt, t = gt - v * nt;
+        const int chunk = item - fr.item_off[gt];
+        const int n_it = fr.item_off[gt + 1] - fr.item_off[gt];
+        const int slot = fr.split_slot[gt];
+        const float kexp = fr.views[v].kexp;
+        const int tx = t % ntx, ty = t / ntx;
+        const int px0 = tx * T, py0 = ty * T;
+        const int tw = min(T, W - px0), th = min(T, H - py0);
+        const int64_t seg1 = fr.offsets[gt + 1];
+        const int64_t e0 = fr.offsets[gt] + (int64_t)chunk * K;
+        const int nrec = (int)(min(seg1, e0 + K) - e0);
+        const int nst = (nrec + kWStage - 1) / kWStage;
+
+        // this lane's pixels: (c * 8 + lc, r * 4 + lr) of the tile; pixels outside the
+        // tile get a centre no support reaches
+        float fx[NC], fy[NR], ar[NR][NC], ag[NR][NC], ab[NR][NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) fx[c] = c * 8 + lc < tw ? (float)(px0 + c * 8 + lc) + 0.5f : kFar;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            fy[r] = r * 4 + lr < th ? (float)(py0 + r * 4 + lr) + 0.5f : kFar;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ar[r][c] = ag[r][c] = ab[r][c] = 0.0f;
+        }
+
+        if (lane == 0 && nrec > 0) {
+            const int c0 = min(kWStage, nrec);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&ws->bar[0], (uint32_t)c0 * 16u);
+            bulk_g2s(ws->buf[0], fr.lists + e0, (uint32_t)c0 * 16u, &ws->bar[0]);
+        }
+        for (int si = 0; si < nst; ++si) {
+            const int cb = si & 1;
+            if (lane == 0 && si + 1 < nst) {
+                const int nb = (si + 1) & 1;
+                const int cn = min(kWStage, nrec - (si + 1) * kWStage);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&ws->bar[nb], (uint32_t)cn * 16u);
+                bulk_g2s(ws->buf[nb], fr.lists + e0 + (int64_t)(si + 1) * kWStage, (uint32_t)cn * 16u,
+                         &ws->bar[nb]);
+            }
+            const bool ok = mbar_wait_bounded(&ws->bar[cb], cb ? phase1 : phase0, kWaitCycles);
+            if (cb) phase1 ^= 1u; else phase0 ^= 1u;
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) atomicExch(&fr.status[kStatTimeout], 1);
+                return;
+            }
+            const int cnt = min(kWStage, nrec - si * kWStage);
+            for (int g = 0; g < cnt; g += 32) {
+                // ---- decode: one record per lane
+                uint32_t mask = 0;
+                if (g + lane < cnt) {
+                    const float4 rec = ws->buf[cb][g + lane];
+                    const float X = rec.x, Y = rec.y, R = rec.z;
+                    const uint32_t code = __float_as_uint(rec.w);
+                    // tight pixel range of the support inside the tile; eps exceeds the
+                    // FP32 rounding of X +- R at any position, so no covered pixel is lost
+                    const float eps = 1e-3f + 2e-6f * (fabsf(X) + fabsf(Y) + R);
+                    const int ilo = max(0, (int)ceilf(clampf(X - R - 0.5f - eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
+                    const int ihi = min(tw - 1, (int)floorf(clampf(X + R - 0.5f + eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
+                    const int jlo = max(0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))) - py0);
+                    const int jhi = min(th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))) - py0);
+                    if (ilo <= ihi && jlo <= jhi) {
+                        if constexpr (kRectDispatch<NR, NC>) {
+                            mask = 1u + (uint32_t)(range_id(jlo >> 2, jhi >> 2, NR) * (NC * (NC + 1) / 2) +
+                                                   range_id(ilo >> 3, ihi >> 3, NC));
+                        } else {
+                            const uint32_t cm = (2u << (ihi >> 3)) - (1u << (ilo >> 3));
+                            const uint64_t rows =
+                                (1ull << (NC * ((jhi >> 2) + 1))) - (1ull << (NC * (jlo >> 2)));
+                            mask = (uint32_t)(rows & ((uint64_t)cm * Shape::kRowRep));
+                        }
+                        const int type = (int)(code >> 24);
+                        const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
+                        const int len = __ldg(&sc.lut_len[type]);
+                        const float f = It * (float)(len - 1);
+                        const int kk = min((int)f, len - 2);
+                        const float tau = f - (float)kk;
+                        const int lo = __ldg(&sc.lut_off[type]) + kk;
+                        const float4 c0 = __ldg(&sc.lut[lo]);
+                        const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                        const float R2 = __fmul_rn(R, R);
+                        float4 *d = reinterpret_cast<float4 *>(&ws->dec[lane]);
+                        d[0] = make_float4(X, Y, R2, __fdividef(kexp, R2));
+                        d[1] = make_float4((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
+                                           (1.0f - tau) * c0.z + tau * c1.z, __uint_as_float(mask));
+                    }
+                }
+                uint32_t live = __ballot_sync(0xffffffffu, mask != 0);
+                __syncwarp();
+                // ---- gather: every live record over the blocks its box overlaps
+                while (live) {
+                    const int k = __ffs(live) - 1;
+                    live &= live - 1;
+                    const float4 pa = *reinterpret_cast<const float4 *>(&ws->dec[k].X);
+                    const float4 pb = *reinterpret_cast<const float4 *>(&ws->dec[k].er);
+                    const uint32_t m = __float_as_uint(pb.w);
+                    if constexpr (kRectDispatch<NR, NC>) {
+                        rect_dispatch<NR, NC>((int)m - 1, fx, fy, ar, ag, ab, pa, pb);
+                    } else {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        if (!(m & (((1u << NC) - 1u) << (r * NC)))) continue;
+                        const float dy = __fsub_rn(fy[r], pa.y);
+                        const float dy2 = __fmul_rn(dy, dy);
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            if (!(m & (1u << (r * NC + c)))) continue;
+                            const float dx = __fsub_rn(fx[c], pa.x);
+                            const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2);
+                            if (d2 < pa.z) {
+                                const float w = ex2_fast(d2 * pa.w);
+                                ar[r][c] += pb.x * w;
+                                ag[r][c] += pb.y * w;
+                                ab[r][c] += pb.z * w;
+                            }
+                        }
+                    }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+
+        // epilogue: final transform of this lane's pixels, or merge of a split tile
+        float *o = out + (int64_t)v * H * W * 3;
+        if (slot < 0) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (r * 4 + lr >= th) continue;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c * 8 + lc >= tw) continue;
+                    float *p = o + ((int64_t)(py0 + r * 4 + lr) * W + px0 + c * 8 + lc) * 3;
+                    p[0] = out_accum ? ar[r][c] : -expm1f(-ar[r][c]);
+                    p[1] = out_accum ? ag[r][c] : -expm1f(-ag[r][c]);
+                    p[2] = out_accum ? ab[r][c] : -expm1f(-ab[r][c]);
+                }
+            }
+        } else {
+            float *scr = fr.scratch + (int64_t)slot * 3 * T * T;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (r * 4 + lr >= th) continue;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c * 8 + lc >= tw) continue;
+                    const int pix = (r * 4 + lr) * T + c * 8 + lc;
+                    if (ar[r][c] != 0.0f) atomicAdd(&scr[pix], ar[r][c]);
+                    if (ag[r][c] != 0.0f) atomicAdd(&scr[T * T + pix], ag[r][c]);
+                    if (ab[r][c] != 0.0f) atomicAdd(&scr[2 * T * T + pix], ab[r][c]);
+                }
+            }
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = (atomicAdd(&fr.tickets[slot], 1) == n_it - 1);
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                const int rowlen = 3 * tw;
+                for (int k = lane; k < th * rowlen; k += 32) {
+                    const int rr = k / rowlen, cc = k - rr * rowlen;
+                    const int col = cc / 3, ch = cc - col * 3;
+                    const float a = __ldcg(&scr[ch * T * T + rr * T + col]);
+                    o[((int64_t)(py0 + rr) * W + px0) * 3 + cc] = out_accum ? a : -expm1f(-a);
+                }
+                __syncwarp();
+                for (int k = lane; k < 3 * T * T; k += 32) scr[k] = 0.0f;
+                if (lane == 0) fr.tickets[slot] = 0;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+typedef void (*SplatFn)(SceneDev, FrameDev, int *, float *, int);
+
+// tiles up to kWarpTileMax px: warp per item; larger tiles: CTA per item
+constexpr int kWarpTileMax = 24;
+static bool warp_kernel(int T) { return T <= kWarpTileMax; }
+
+static SplatFn splat_fn(int T) {
+    if (warp_kernel(T)) {
+        if (T <= 8) return k_splat_warp<2, 1>;
+        if (T <= 16) return k_splat_warp<4, 2>;
+        return k_splat_warp<6, 3>;
+    }
+    switch (block_cols(T)) {
+        case 1: return k_splat<1, 1>;
+        case 2: return k_splat<1, 2>;
+        case 3: return k_splat<1, 3>;
+        case 4: return k_splat<1, 4>;
         case 5: return k_splat<2, 5>;
         case 6: return k_splat<2, 6>;
         case 7: return k_splat<2, 7>;
@@ -298,23 +614,28 @@ static SplatFn splat_fn(int T) {
     }
 }
 
+static size_t splat_smem(int T) { return warp_kernel(T) ? sizeof(WarpSmem) * kWarpsPerCta : splat_smem_bytes(T); }
+static int splat_cta_threads(int T) { return warp_kernel(T) ? kWarpsPerCta * 32 : kSplatThreads; }
+
 int splat_blocks_per_sm(int T) {
-    const size_t smem = splat_smem_bytes(T);
+    const size_t smem = splat_smem(T);
     SplatFn fn = splat_fn(T);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kSplatThreads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, splat_cta_threads(T), smem) != cudaSuccess) return 0;
     return nb;
 }
 
+int splat_workers_per_sm(int T) { return splat_blocks_per_sm(T) * (warp_kernel(T) ? kWarpsPerCta : 1); }
+
 cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, float *out, int out_accum,
                          int grid, cudaStream_t st) {
-    const size_t smem = splat_smem_bytes(fr.T);
+    const size_t smem = splat_smem(fr.T);
     SplatFn fn = splat_fn(fr.T);
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    fn<<<grid, kSplatThreads, smem, st>>>(sc, fr, queue, out, out_accum);
+    fn<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum);
     return cudaGetLastError();
 }
 

@@ -489,7 +489,7 @@ static splotch_status choose_tile(int W, int H, int requested, int *T) {
         *T = requested;
         return SPLOTCH_OK;
     }
-    for (int t = 32; t <= kMaxTile; t += 8)
+    for (int t = 16; t <= kMaxTile; t += 8)
         if (n_tiles_for(W, H, t) <= kMaxTiles) {
             *T = t;
             return SPLOTCH_OK;
@@ -551,7 +551,9 @@ static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_ti
     const int64_t unit = (int64_t)kThreads * vec;
     const int64_t n_units = std::max<int64_t>(1, (sc->n + unit - 1) / unit);
     const int groups = (V + fh.G - 1) / fh.G;
-    int64_t target = std::max<int64_t>(1, (4 * n_sm + groups - 1) / groups);
+    // two whole waves of the binning kernels over all view groups
+    const int occ = bin_ctas_per_sm(sc->storage, sizeof(int) * (size_t)fh.G * n_tiles);
+    int64_t target = std::max<int64_t>(1, (2ll * n_sm * occ + groups - 1) / groups);
     target = std::min(target, n_units);
     const int64_t max_chunks = std::max<int64_t>(1, rel_budget / (4ll * V * n_tiles));
     int64_t nch = std::min(target, max_chunks);
@@ -616,11 +618,12 @@ static FrameDev frame_dev(const FrameHost &fh, char *fixed, char *var) {
 
 static int splat_grid(int dev, int T, int items) {
     const int bps = std::max(1, splat_blocks_per_sm(T));
+    const int per_cta = std::max(1, splat_workers_per_sm(T) / bps);
     const int g = sm_count(dev) * bps;
-    return std::max(1, std::min(g, std::max(1, items)));
+    return std::max(1, std::min(g, (std::max(1, items) + per_cta - 1) / per_cta));
 }
 
-static int target_items(int dev, int T) { return sm_count(dev) * std::max(1, splat_blocks_per_sm(T)) * 4; }
+static int target_items(int dev, int T) { return sm_count(dev) * std::max(1, splat_workers_per_sm(T)) * 4; }
 static const int kMinItemPairs = 2048;
 
 struct RenderSetup {

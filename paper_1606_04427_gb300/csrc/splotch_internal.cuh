@@ -280,6 +280,8 @@ cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, 
 cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, float *out,
                          int out_accum, int grid, cudaStream_t st);
 int splat_blocks_per_sm(int T);
+int splat_workers_per_sm(int T);
+int bin_ctas_per_sm(int storage, size_t smem);
 size_t splat_smem_bytes(int T);
 cudaError_t launch_selftest_wait(long long limit, int *result, cudaStream_t st);
 cudaError_t launch_final(float *a, int64_t count, cudaStream_t st);

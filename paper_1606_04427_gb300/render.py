@@ -44,6 +44,15 @@ class RenderParams:
         return p
 
 
+def default_tile(width: int, height: int) -> int:
+    """Tile edge the library picks for tile = 0: 16 px, or the smallest edge above it in
+    steps of 8 that keeps the image within 16384 tiles."""
+    T = 16
+    while ((width + T - 1) // T) * ((height + T - 1) // T) > 16384 and T < 64:
+        T += 8
+    return T
+
+
 def _stream_handle(stream) -> int:
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -194,9 +203,7 @@ class Scene:
         T = p.tile if p.tile > 0 else None
         c = _lib.camera_c(cam)
         if T is None:
-            T = 32
-            while ((cam.width + T - 1) // T) * ((cam.height + T - 1) // T) > 16384 and T < 64:
-                T += 8
+            T = default_tile(cam.width, cam.height)
         nt = ((cam.width + T - 1) // T) * ((cam.height + T - 1) // T)
         counts = torch.empty(nt, dtype=torch.int32, device="cuda")
         offsets = torch.empty(nt + 1, dtype=torch.int64, device="cuda")
