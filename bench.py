@@ -159,7 +159,10 @@ SPLAT_FLOPS_PER_PAIR = 10
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel, from one ncu capture per workload; valid only while the kernel source hashes
 # to the recorded digest, else reported as null.
-TRAFFIC = {}
+TRAFFIC = {
+    "two_species_f16": {"bytes_per_launch": 3.29e9 + 60.06e6, "digest": "de447a9d5d4c06f4",
+                        "kernel": "k_splat_warp<4,2>", "tile": 16},
+}
 
 
 def kernel_digest():
@@ -242,6 +245,118 @@ def run_reference(args):
     return 0
 
 
+def _timed_clocks(fn, steps, stream, local):
+    """Run fn() steps times between CUDA events on `stream`, sampling clocks; returns
+    (ms per step, clocks)."""
+    import torch
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    return ev0.elapsed_time(ev1) / steps, clk
+
+
+def run_batched(args):
+    """64 orbit views of 20 M clustered particles (FP16 storage) at 1024 x 1024 rendered
+    by one plan replayed as a CUDA graph; tile and particles per CTA from the autotuner."""
+    import torch
+    from paper_1606_04427_gb300 import autotune, build, render, synth
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    beta = load_brightness().get("batched", [1.0])
+    ps = _cached(os.environ.get("SPLOTCH_SYNTH_CACHE"), "batched",
+                 lambda: synth.clustered_set(20_000_000, 3)).with_brightness(beta)
+    cams = synth.orbit_cameras(64, 1024, 1024)
+    scene = render.Scene(ps, "f16")
+    t0 = time.perf_counter()
+    tuned = autotune.tune(scene, cams, tiles=(8, 16, 24, 32, 40, 48, 64), blocks=(0, 262144), repeats=2)
+    sweep_s = time.perf_counter() - t0
+    plan = render.Plan(scene, cams, tuned["params"], graph=True)
+    out = plan.new_output()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.launch(out)
+    plan.check()
+    ms, clk = _timed_clocks(lambda: plan.launch(out), args.steps, stream, local)
+    plan.check()
+    info = plan.info()
+    V, n = len(cams), ps.n
+    units = work_units("batched_f16")
+    peaks, _ = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    line = {"metric": METRIC, "value": V * n / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched_orbit64_clustered20M_f16", "n_particles": n, "views": V,
+                       "image": [1024, 1024], "storage": "f16", "accumulation": "f32",
+                       "tile": info["tile"], "block_particles": tuned["params"].block_particles,
+                       "l2": "inputs larger than L2: 0.20 GB of attributes + 0.81 GB of images per step"},
+            "frames_per_s": V / (ms * 1e-3), "autotune": {"sweep_s": sweep_s, "table": tuned["table"]},
+            "plan_device_bytes": info["device_bytes"], "gpu_launches": 4 * args.steps, "clocks": clk}
+    if units:
+        flops = units["pixel_pairs"] * SPLAT_FLOPS_PER_PAIR
+        line["roofline"] = {"bound": "alu", "kernel": "whole batch (upper bound on the splat's time)",
+                            "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                            "frac": flops / (ms * 1e-3) / 1e12 / fp32_peak, "traffic": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args):
+    """Poisson render requests over 8 resident FP16 clustered sets of 1 M to 200 M
+    particles, images 512^2 to 4096^2, random cameras; continuous batching with admission
+    by HBM footprint.  Saturated throughput first (all requests at once), then traces at
+    0.5, 0.8 and 1.0 of it; latency is arrival to completion."""
+    import torch
+    from paper_1606_04427_gb300 import build, render, serve, synth
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    beta = load_brightness().get("served")
+    sizes = synth.served_set_sizes()
+    cache = os.environ.get("SPLOTCH_SYNTH_CACHE")
+    scenes = []
+    for k, n in enumerate(sizes):
+        ps = _cached(cache, f"served{k}", lambda n=n, k=k: synth.clustered_set(n, 4 + k))
+        scenes.append(render.Scene(ps.with_brightness([beta[k]] if beta else [1.0]), "f16"))
+        del ps
+    rng = np.random.default_rng(4)
+    nreq = args.served_requests
+    srv = serve.Server(scenes, slots=args.slots)
+    try:
+        warm = synth.poisson_requests(rng, 16, 1e6, len(scenes))
+        srv.run_trace(warm)
+        burst = synth.poisson_requests(rng, nreq, 1e9, len(scenes))
+        sat = srv.run_trace(burst)
+        res = {"saturated": sat}
+        for lam in (0.5, 0.8, 1.0):
+            reqs = synth.poisson_requests(rng, nreq, lam * sat["requests_per_s"], len(scenes))
+            res[f"lambda_{lam}"] = srv.run_trace(reqs)
+        errors = list(srv.errors)
+        peak = srv.peak_reserved
+    finally:
+        srv.close()
+    r08 = res["lambda_0.8"]
+    line = {"metric": METRIC, "value": sat["mparticles_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": nreq, "warmup": 16, "ms_per_step": 1e3 / sat["requests_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served_8sets_1M-200M_f16", "set_sizes": sizes, "images": [512, 4096],
+                       "slots": args.slots, "requests_per_trace": nreq, "storage": "f16"},
+            "served": res, "p50_ms": r08["p50_ms"], "p99_ms": r08["p99_ms"], "peak_reserved_bytes": peak,
+            "errors": errors[:5]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def max_over_ranks(value: float) -> float:
     """The largest value over all ranks (the step time of the slowest GPU); a no-op
     outside torch.distributed."""
@@ -264,7 +379,7 @@ def config_dict(name, ps, cam, storage, tile):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="two_species_f16")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
@@ -272,9 +387,15 @@ def main():
     ap.add_argument("--ref-particles", type=int, default=2_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--served-requests", type=int, default=400)
+    ap.add_argument("--slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
 
     import torch
     from paper_1606_04427_gb300 import build, render
@@ -295,6 +416,7 @@ def main():
 
     ps, cam, storage = make_workload(args.workload)
     params = render.RenderParams(tile=args.tile)
+    tile = args.tile or render.default_tile(cam.width, cam.height)
     stream = torch.cuda.current_stream()
     scene = render.Scene(ps, storage)
     out = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
@@ -390,7 +512,8 @@ def main():
     dom = max(kms, key=lambda k: kms[k])
     digest = kernel_digest()
     tr = TRAFFIC.get(args.workload)
-    traffic = tr["bytes_per_launch"] if (tr and tr["digest"] == digest and dom == "splat") else None
+    traffic = (tr["bytes_per_launch"] if (tr and tr["digest"] == digest and dom == "splat" and tr["tile"] == tile)
+               else None)
     frame_alg = n * 5 * b + WH * 12
     if dom == "splat" and "frac" in splat:
         roof = {"bound": "alu", "kernel": "k_splat", "achieved": splat["achieved_tflops"], "peak": fp32_peak,
@@ -409,7 +532,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(args.workload, ps, cam, storage, args.tile or None),
+            "config": config_dict(args.workload, ps, cam, storage, tile),
             "frames_per_s": world * 1e3 / ms,
             "kernels_ms": kms, "kernels": kern, "pairs": P, "work_items": sizes["items"],
             "split_tiles": sizes["splits"], "work_units": units, "roofline": roof,

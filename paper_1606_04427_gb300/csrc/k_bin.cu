@@ -12,7 +12,28 @@
 //             (particle, tile) pair into its tile segment.
 #include "splotch_internal.cuh"
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 namespace spl {
+
+cudaError_t ensure_smem_limit(const void *kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> set;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = set[std::make_pair(kernel, dev)];
+    if (cur >= bytes) return cudaSuccess;
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (err == cudaSuccess) cur = bytes;
+    return err;
+}
+
+// largest tile histogram: G x n_tiles <= kMaxTiles counters
+constexpr size_t kBinSmemMax = sizeof(int) * (size_t)kMaxTiles;
 
 // ---------------------------------------------------------------------------------------
 // Scene preparation (Section 2.1: ranging, normalisation, optional logarithm).
@@ -200,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) k_count(SceneDev sc, FrameDev fr) {
 
 template <int S> static cudaError_t count_impl(const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
     const size_t smem = (size_t)fr.G * fr.n_tiles * sizeof(int);
-    cudaError_t err = cudaFuncSetAttribute(k_count<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = ensure_smem_limit((const void *)k_count<S>, kBinSmemMax);
     if (err != cudaSuccess) return err;
     dim3 grid(fr.n_chunks, (fr.V + fr.G - 1) / fr.G);
     k_count<S><<<grid, kThreads, smem, st>>>(sc, fr);
@@ -451,7 +472,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
 template <int S> static cudaError_t scatter_impl(const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
     const size_t smem = (size_t)fr.G * fr.n_tiles * sizeof(int);
     cudaError_t err =
-        cudaFuncSetAttribute(k_scatter<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax);
     if (err != cudaSuccess) return err;
     dim3 grid(fr.n_chunks, (fr.V + fr.G - 1) / fr.G);
     k_scatter<S><<<grid, kThreads, smem, st>>>(sc, fr);
@@ -468,8 +489,8 @@ cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, 
 // smaller of count and scatter, so both run their chunks in whole waves).
 template <int S> static int bin_occupancy(size_t smem) {
     int a = 0, b = 0;
-    if (cudaFuncSetAttribute(k_count<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_scatter<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (ensure_smem_limit((const void *)k_count<S>, kBinSmemMax) != cudaSuccess ||
+        ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_count<S>, kThreads, smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scatter<S>, kThreads, smem) != cudaSuccess) {
         cudaGetLastError();

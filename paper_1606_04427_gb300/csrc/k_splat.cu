@@ -620,8 +620,7 @@ static int splat_cta_threads(int T) { return warp_kernel(T) ? kWarpsPerCta * 32 
 int splat_blocks_per_sm(int T) {
     const size_t smem = splat_smem(T);
     SplatFn fn = splat_fn(T);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
+    if (ensure_smem_limit((const void *)fn, smem) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, splat_cta_threads(T), smem) != cudaSuccess) return 0;
     return nb;
@@ -633,7 +632,7 @@ cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, flo
                          int grid, cudaStream_t st) {
     const size_t smem = splat_smem(fr.T);
     SplatFn fn = splat_fn(fr.T);
-    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = ensure_smem_limit((const void *)fn, smem);
     if (err != cudaSuccess) return err;
     fn<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum);
     return cudaGetLastError();

@@ -282,6 +282,11 @@ cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, flo
 int splat_blocks_per_sm(int T);
 int splat_workers_per_sm(int T);
 int bin_ctas_per_sm(int storage, size_t smem);
+
+// Raise a kernel's dynamic shared-memory limit on the current device to at least
+// `bytes`, once per (kernel, device).  The limit is process-wide state: renders on other
+// host threads launch the same kernels, so it is only ever raised, never set per launch.
+cudaError_t ensure_smem_limit(const void *kernel, size_t bytes);
 size_t splat_smem_bytes(int T);
 cudaError_t launch_selftest_wait(long long limit, int *result, cudaStream_t st);
 cudaError_t launch_final(float *a, int64_t count, cudaStream_t st);

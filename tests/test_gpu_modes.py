@@ -118,3 +118,36 @@ def test_shards_sum_to_the_whole_frame():
     shard.final_transform_(summed)
     ref = oracle.final(oracle.render(ps, cam))
     assert np.abs(summed.cpu().numpy() - ref).max() <= 1e-4
+
+
+def test_concurrent_renders_of_different_image_sizes():
+    """Host threads rendering different image sizes at once (each on its own stream):
+    the kernels' per-launch shared-memory needs differ, and no launch may see another
+    thread's setting.  Every image equals the same render made alone."""
+    import threading
+    ps = synth.clustered_set(60000, 9, grid=64).with_brightness([0.05])
+    sc = render.Scene(ps, "f32")
+    sizes = [(64, 48), (512, 512), (1024, 768), (200, 130), (2048, 1024), (96, 96)]
+    cams = [synth.front_camera(w, h) for w, h in sizes]
+    alone = [sc.render(c, render.RenderParams(sync=True)).cpu() for c in cams]
+    errors, results = [], {}
+
+    def work(k):
+        try:
+            st = torch.cuda.Stream()
+            for rep in range(6):
+                j = (k + rep) % len(cams)
+                img = sc.render(cams[j], render.RenderParams(sync=True), stream=st)
+                results[(k, rep)] = (j, img.cpu())
+        except Exception as e:  # collected and asserted below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=120)
+    assert not errors, errors
+    assert len(results) == 24
+    for (k, rep), (j, img) in results.items():
+        assert torch.abs(img - alone[j]).max().item() <= 1e-4, (k, rep, sizes[j])
