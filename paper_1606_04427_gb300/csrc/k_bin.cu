@@ -35,6 +35,7 @@ cudaError_t ensure_smem_limit(const void *kernel, size_t bytes) {
 // largest tile histogram: G x n_tiles <= kMaxTiles counters
 constexpr size_t kBinSmemMax = sizeof(int) * (size_t)kMaxTiles;
 
+
 // ---------------------------------------------------------------------------------------
 // Scene preparation (Section 2.1: ranging, normalisation, optional logarithm).
 
@@ -140,6 +141,50 @@ cudaError_t launch_prepare(const float *x, const float *y, const float *z, const
 // ---------------------------------------------------------------------------------------
 // k_count: raster a chunk of particles for up to G views and count tile memberships.
 
+// Bin one particle for every view of the group: 2 x 2 candidate tiles or fewer by this
+// lane, larger candidate boxes by the whole warp (one such particle at a time).  Called by
+// all lanes of the warp together.
+__device__ __forceinline__ void count_particle(bool valid, float x, float y, float z, float h,
+                                               const ViewParams *s_view, int g_n, int *s_hist, int nt,
+                                               int lane) {
+    for (int g = 0; g < g_n; ++g) {
+        const ViewParams &vp = s_view[g];
+        int *hist = s_hist + g * nt;
+        Raster r;
+        int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+        if (valid && raster_one(vp, x, y, z, h, r)) {
+            tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
+            ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
+        }
+        const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
+        if (small) {
+            const bool m00 = tile_member(vp, r.X, r.Y, r.R, tx0, ty0);
+            const bool m10 = tx1 > tx0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty0);
+            const bool m01 = ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx0, ty1);
+            const bool m11 = tx1 > tx0 && ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty1);
+            const int t00 = ty0 * vp.ntx + tx0;
+            if (m00) atomicAdd(&hist[t00], 1);
+            if (m10) atomicAdd(&hist[t00 + 1], 1);
+            if (m01) atomicAdd(&hist[t00 + vp.ntx], 1);
+            if (m11) atomicAdd(&hist[t00 + vp.ntx + 1], 1);
+        }
+        uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const float bX = __shfl_sync(0xffffffffu, r.X, src), bY = __shfl_sync(0xffffffffu, r.Y, src);
+            const float bR = __shfl_sync(0xffffffffu, r.R, src);
+            const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
+            const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
+            const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
+            for (int k = lane; k < ncand; k += 32) {
+                const int ty = by0 + k / bw, tx = bx0 + k % bw;
+                if (tile_member(vp, bX, bY, bR, tx, ty)) atomicAdd(&hist[ty * vp.ntx + tx], 1);
+            }
+        }
+    }
+}
+
 template <int S>
 __global__ void __launch_bounds__(kThreads) k_count(SceneDev sc, FrameDev fr) {
     extern __shared__ int s_hist[];  // [g_n][n_tiles]
@@ -154,58 +199,26 @@ __global__ void __launch_bounds__(kThreads) k_count(SceneDev sc, FrameDev fr) {
 
     const int64_t s = (int64_t)b * fr.chunk;
     const int64_t e = min(sc.n, s + fr.chunk);
-    // the next particle's attributes are loaded before this one is binned, so a load is
-    // always in flight behind the shared-memory work.  The loop runs warp-uniformly (a
-    // lane past the chunk end idles) so that particles whose candidate box is larger than
-    // 2 x 2 tiles can be binned by the whole warp, one such particle at a time.
+    // Two particles per thread per iteration, A and B, each in its own registers: A's next
+    // attributes are loaded as soon as A is binned and stay in flight while B is binned
+    // (and the other way round), hiding DRAM latency.  The loop runs warp-uniformly (a lane
+    // past the chunk end idles) because large particles are binned by the whole warp.
     const int lane = threadIdx.x & 31;
+    const int64_t stride = blockDim.x;
     int64_t i = s + threadIdx.x;
-    float nx = 0.0f, ny = 0.0f, nz = 0.0f, nh = 0.0f;
-    if (i < e) nx = load1<S>(sc.x, i), ny = load1<S>(sc.y, i), nz = load1<S>(sc.z, i), nh = load1<S>(sc.h, i);
-    for (; i - lane < e; i += blockDim.x) {
-        const bool valid = i < e;
-        const float x = nx, y = ny, z = nz, h = nh;
-        const int64_t inext = i + blockDim.x;
-        if (inext < e)
-            nx = load1<S>(sc.x, inext), ny = load1<S>(sc.y, inext), nz = load1<S>(sc.z, inext),
-            nh = load1<S>(sc.h, inext);
-        for (int g = 0; g < g_n; ++g) {
-            const ViewParams &vp = s_view[g];
-            int *hist = s_hist + g * nt;
-            Raster r;
-            int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-            if (valid && raster_one(vp, x, y, z, h, r)) {
-                tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
-                ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
-            }
-            const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
-            if (small) {
-                // at most 2 x 2 candidate tiles: the common case, tested without loops
-                const bool m00 = tile_member(vp, r.X, r.Y, r.R, tx0, ty0);
-                const bool m10 = tx1 > tx0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty0);
-                const bool m01 = ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx0, ty1);
-                const bool m11 = tx1 > tx0 && ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty1);
-                const int t00 = ty0 * vp.ntx + tx0;
-                if (m00) atomicAdd(&hist[t00], 1);
-                if (m10) atomicAdd(&hist[t00 + 1], 1);
-                if (m01) atomicAdd(&hist[t00 + vp.ntx], 1);
-                if (m11) atomicAdd(&hist[t00 + vp.ntx + 1], 1);
-            }
-            uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
-            while (big) {
-                const int src = __ffs(big) - 1;
-                big &= big - 1;
-                const float bX = __shfl_sync(0xffffffffu, r.X, src), bY = __shfl_sync(0xffffffffu, r.Y, src);
-                const float bR = __shfl_sync(0xffffffffu, r.R, src);
-                const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
-                const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
-                const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
-                for (int k = lane; k < ncand; k += 32) {
-                    const int ty = by0 + k / bw, tx = bx0 + k % bw;
-                    if (tile_member(vp, bX, bY, bR, tx, ty)) atomicAdd(&hist[ty * vp.ntx + tx], 1);
-                }
-            }
-        }
+    float ax = 0.0f, ay = 0.0f, az = 0.0f, ah = 0.0f, bx = 0.0f, by = 0.0f, bz = 0.0f, bh = 0.0f;
+    if (i < e) ax = load1<S>(sc.x, i), ay = load1<S>(sc.y, i), az = load1<S>(sc.z, i), ah = load1<S>(sc.h, i);
+    if (i + stride < e)
+        bx = load1<S>(sc.x, i + stride), by = load1<S>(sc.y, i + stride), bz = load1<S>(sc.z, i + stride),
+        bh = load1<S>(sc.h, i + stride);
+    for (; i - lane < e; i += 2 * stride) {
+        count_particle(i < e, ax, ay, az, ah, s_view, g_n, s_hist, nt, lane);
+        const int64_t ia = i + 2 * stride;
+        if (ia < e) ax = load1<S>(sc.x, ia), ay = load1<S>(sc.y, ia), az = load1<S>(sc.z, ia), ah = load1<S>(sc.h, ia);
+        if (i + stride - lane >= e) break;
+        count_particle(i + stride < e, bx, by, bz, bh, s_view, g_n, s_hist, nt, lane);
+        const int64_t ib = i + 3 * stride;
+        if (ib < e) bx = load1<S>(sc.x, ib), by = load1<S>(sc.y, ib), bz = load1<S>(sc.z, ib), bh = load1<S>(sc.h, ib);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < g_n * nt; k += blockDim.x) {
@@ -370,6 +383,79 @@ cudaError_t launch_scan(const FrameDev &fr, int target_items, int kmin, cudaStre
 // k_scatter: same chunks as k_count; every (particle, tile) pair becomes a record
 // {X, Y, R, type << 24 | 24-bit normalised intensity} in its tile segment.
 
+// Write the records of one particle for every view of the group (same split between
+// lane and warp as count_particle).  Called by all lanes of the warp together.
+__device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x, float y, float z, float h,
+                                                 float code, const ViewParams *s_view, const int64_t *s_vbase,
+                                                 int g_n, int *s_cur, int nt, const FrameDev &fr, int lane) {
+    for (int g = 0; g < g_n; ++g) {
+        const ViewParams &vp = s_view[g];
+        int *cur = s_cur + g * nt;
+        float4 *lists = fr.lists + s_vbase[g];
+        int *pids = fr.pids ? fr.pids + s_vbase[g] : nullptr;
+        Raster r;
+        int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+        if (valid && raster_one(vp, x, y, z, h, r)) {
+            tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
+            ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
+        }
+        const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
+        if (small) {
+            // all cursor reservations first, then the stores: one atomic latency per
+            // particle instead of one per tile
+            const float4 rec = make_float4(r.X, r.Y, r.R, code);
+            const int t00 = ty0 * vp.ntx + tx0;
+            const bool m00 = tile_member(vp, r.X, r.Y, r.R, tx0, ty0);
+            const bool m10 = tx1 > tx0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty0);
+            const bool m01 = ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx0, ty1);
+            const bool m11 = tx1 > tx0 && ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty1);
+            const int p00 = m00 ? atomicAdd(&cur[t00], 1) : 0;
+            const int p10 = m10 ? atomicAdd(&cur[t00 + 1], 1) : 0;
+            const int p01 = m01 ? atomicAdd(&cur[t00 + vp.ntx], 1) : 0;
+            const int p11 = m11 ? atomicAdd(&cur[t00 + vp.ntx + 1], 1) : 0;
+            if (m00) lists[p00] = rec;
+            if (m10) lists[p10] = rec;
+            if (m01) lists[p01] = rec;
+            if (m11) lists[p11] = rec;
+            if (pids) {
+                if (m00) pids[p00] = (int)i;
+                if (m10) pids[p10] = (int)i;
+                if (m01) pids[p01] = (int)i;
+                if (m11) pids[p11] = (int)i;
+            }
+        }
+        uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const float bX = __shfl_sync(0xffffffffu, r.X, src), bY = __shfl_sync(0xffffffffu, r.Y, src);
+            const float bR = __shfl_sync(0xffffffffu, r.R, src);
+            const float bcode = __shfl_sync(0xffffffffu, code, src);
+            const int bid = __shfl_sync(0xffffffffu, (int)i, src);
+            const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
+            const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
+            const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
+            const float4 rec = make_float4(bX, bY, bR, bcode);
+            for (int k = lane; k < ncand; k += 32) {
+                const int ty = by0 + k / bw, tx = bx0 + k % bw;
+                if (tile_member(vp, bX, bY, bR, tx, ty)) {
+                    const int t = ty * vp.ntx + tx;
+                    const int pos = atomicAdd(&cur[t], 1);
+                    lists[pos] = rec;
+                    if (pids) pids[pos] = bid;
+                }
+            }
+        }
+    }
+}
+
+// Record code of a particle: species in the top 8 bits, normalised intensity in 24 bits.
+__device__ __forceinline__ float record_code(int type, float itn) {
+    uint32_t q = __float2uint_rn(__fmul_rn(itn, (float)kCodeMax));
+    q = min(q, kCodeMax);
+    return __uint_as_float(((uint32_t)type << 24) | q);
+}
+
 template <int S>
 __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) {
     if (fr.status[kStatOverflow]) return;
@@ -397,75 +483,38 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
 
     const int64_t s = (int64_t)b * fr.chunk;
     const int64_t e = min(sc.n, s + fr.chunk);
-    int type = 0;
+    // two particles per thread per iteration in separate registers (see k_count)
     const int lane = threadIdx.x & 31;
+    const int64_t stride = blockDim.x;
+    int type = 0;
     int64_t i = s + threadIdx.x;
-    float nx = 0.0f, ny = 0.0f, nz = 0.0f, nh = 0.0f, ni = 0.0f;
+    float ax = 0.0f, ay = 0.0f, az = 0.0f, ah = 0.0f, ai = 0.0f;
+    float bx = 0.0f, by = 0.0f, bz = 0.0f, bh = 0.0f, bi = 0.0f;
     if (i < e)
-        nx = load1<S>(sc.x, i), ny = load1<S>(sc.y, i), nz = load1<S>(sc.z, i), nh = load1<S>(sc.h, i),
-        ni = load1<S>(sc.it, i);
-    for (; i - lane < e; i += blockDim.x) {
-        const bool valid = i < e;
-        const float x = nx, y = ny, z = nz, h = nh, itn = ni;
-        const int64_t inext = i + blockDim.x;
-        if (inext < e)
-            nx = load1<S>(sc.x, inext), ny = load1<S>(sc.y, inext), nz = load1<S>(sc.z, inext),
-            nh = load1<S>(sc.h, inext), ni = load1<S>(sc.it, inext);
-        if (valid)
+        ax = load1<S>(sc.x, i), ay = load1<S>(sc.y, i), az = load1<S>(sc.z, i), ah = load1<S>(sc.h, i),
+        ai = load1<S>(sc.it, i);
+    if (i + stride < e)
+        bx = load1<S>(sc.x, i + stride), by = load1<S>(sc.y, i + stride), bz = load1<S>(sc.z, i + stride),
+        bh = load1<S>(sc.h, i + stride), bi = load1<S>(sc.it, i + stride);
+    for (; i - lane < e; i += 2 * stride) {
+        if (i < e)
             while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
-        uint32_t q = __float2uint_rn(__fmul_rn(itn, (float)kCodeMax));
-        q = min(q, kCodeMax);
-        const float code = __uint_as_float(((uint32_t)type << 24) | q);
-        for (int g = 0; g < g_n; ++g) {
-            const ViewParams &vp = s_view[g];
-            int *cur = s_cur + g * nt;
-            float4 *lists = fr.lists + s_vbase[g];
-            int *pids = fr.pids ? fr.pids + s_vbase[g] : nullptr;
-            Raster r;
-            int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-            if (valid && raster_one(vp, x, y, z, h, r)) {
-                tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
-                ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
-            }
-            const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
-            if (small) {
-                const float4 rec = make_float4(r.X, r.Y, r.R, code);
-                const int t00 = ty0 * vp.ntx + tx0;
-#pragma unroll
-                for (int qd = 0; qd < 4; ++qd) {
-                    const int dx = qd & 1, dy = qd >> 1;
-                    if ((dx && tx1 == tx0) || (dy && ty1 == ty0)) continue;
-                    if (!tile_member(vp, r.X, r.Y, r.R, tx0 + dx, ty0 + dy)) continue;
-                    const int t = t00 + dy * vp.ntx + dx;
-                    const int pos = atomicAdd(&cur[t], 1);
-                    lists[pos] = rec;
-                    if (pids) pids[pos] = (int)i;
-                }
-            }
-            // particles with more than 2 x 2 candidate tiles: the whole warp bins each one
-            uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
-            while (big) {
-                const int src = __ffs(big) - 1;
-                big &= big - 1;
-                const float bX = __shfl_sync(0xffffffffu, r.X, src), bY = __shfl_sync(0xffffffffu, r.Y, src);
-                const float bR = __shfl_sync(0xffffffffu, r.R, src);
-                const float bcode = __shfl_sync(0xffffffffu, code, src);
-                const int bid = __shfl_sync(0xffffffffu, (int)i, src);
-                const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
-                const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
-                const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
-                const float4 rec = make_float4(bX, bY, bR, bcode);
-                for (int k = lane; k < ncand; k += 32) {
-                    const int ty = by0 + k / bw, tx = bx0 + k % bw;
-                    if (tile_member(vp, bX, bY, bR, tx, ty)) {
-                        const int t = ty * vp.ntx + tx;
-                        const int pos = atomicAdd(&cur[t], 1);
-                        lists[pos] = rec;
-                        if (pids) pids[pos] = bid;
-                    }
-                }
-            }
-        }
+        scatter_particle(i < e, i, ax, ay, az, ah, record_code(type, ai), s_view, s_vbase, g_n, s_cur, nt, fr,
+                         lane);
+        const int64_t ia = i + 2 * stride;
+        if (ia < e)
+            ax = load1<S>(sc.x, ia), ay = load1<S>(sc.y, ia), az = load1<S>(sc.z, ia), ah = load1<S>(sc.h, ia),
+            ai = load1<S>(sc.it, ia);
+        const int64_t j = i + stride;
+        if (j - lane >= e) break;
+        if (j < e)
+            while (type + 1 < sc.n_types && j >= s_tb[type + 1]) ++type;
+        scatter_particle(j < e, j, bx, by, bz, bh, record_code(type, bi), s_view, s_vbase, g_n, s_cur, nt, fr,
+                         lane);
+        const int64_t ib = i + 3 * stride;
+        if (ib < e)
+            bx = load1<S>(sc.x, ib), by = load1<S>(sc.y, ib), bz = load1<S>(sc.z, ib), bh = load1<S>(sc.h, ib),
+            bi = load1<S>(sc.it, ib);
     }
 }
 

@@ -299,9 +299,10 @@ struct __align__(16) WRec {
 
 struct __align__(16) WarpSmem {
     float4 buf[2][kWStage];
-    WRec dec[32];
+    WRec dec[kWStage];          // decoded records of the stage
+    int cnt[32];                // records per block rectangle
+    unsigned char ord[kWStage]; // stage records grouped by block rectangle
     uint64_t bar[2];
-    uint64_t pad;
 };
 
 template <int NR, int NC>
@@ -383,6 +384,54 @@ __device__ __forceinline__ void rect_dispatch(int id, const float (&fx)[NC], con
 template <int NR, int NC>
 constexpr bool kRectDispatch = (NR == 2 && NC == 1) || (NR == 4 && NC == 2);
 
+// All records of one block rectangle, taken from the grouped order: the jump to the
+// rectangle's code is made once for the group.
+template <int NR, int NC, int R0, int R1, int C0, int C1>
+__device__ __forceinline__ void rect_run(const WarpSmem *ws, int j0, int n, const float (&fx)[NC],
+                                         const float (&fy)[NR], float (&ar)[NR][NC], float (&ag)[NR][NC],
+                                         float (&ab)[NR][NC]) {
+    // not unrolled: 30 copies of an unrolled loop overflow the instruction cache
+#pragma unroll 1
+    for (int j = j0; j < j0 + n; ++j) {
+        const int k = ws->ord[j];
+        const float4 pa = *reinterpret_cast<const float4 *>(&ws->dec[k].X);
+        const float4 pb = *reinterpret_cast<const float4 *>(&ws->dec[k].er);
+        rect_splat<NR, NC, R0, R1, C0, C1>(fx, fy, ar, ag, ab, pa, pb);
+    }
+}
+
+#define SPL_RUN(R0, R1, C0, C1)                                                               \
+    case range_id(R0, R1, NR) * (NC * (NC + 1) / 2) + range_id(C0, C1, NC):                  \
+        rect_run<NR, NC, R0, R1, C0, C1>(ws, j0, n, fx, fy, ar, ag, ab);                      \
+        break;
+#define SPL_RUNS4(C0, C1)                                                                      \
+    SPL_RUN(0, 0, C0, C1) SPL_RUN(0, 1, C0, C1) SPL_RUN(0, 2, C0, C1) SPL_RUN(0, 3, C0, C1)     \
+    SPL_RUN(1, 1, C0, C1) SPL_RUN(1, 2, C0, C1) SPL_RUN(1, 3, C0, C1) SPL_RUN(2, 2, C0, C1)     \
+    SPL_RUN(2, 3, C0, C1) SPL_RUN(3, 3, C0, C1)
+
+template <int NR, int NC>
+__device__ __forceinline__ void run_dispatch(int id, const WarpSmem *ws, int j0, int n, const float (&fx)[NC],
+                                             const float (&fy)[NR], float (&ar)[NR][NC], float (&ag)[NR][NC],
+                                             float (&ab)[NR][NC]) {
+    if constexpr (NR == 2 && NC == 1) {
+        switch (id) {
+            SPL_RUN(0, 0, 0, 0)
+            SPL_RUN(0, 1, 0, 0)
+            SPL_RUN(1, 1, 0, 0)
+            default: break;
+        }
+    } else if constexpr (NR == 4 && NC == 2) {
+        switch (id) {
+            SPL_RUNS4(0, 0)
+            SPL_RUNS4(0, 1)
+            SPL_RUNS4(1, 1)
+            default: break;
+        }
+    }
+}
+#undef SPL_RUNS4
+#undef SPL_RUN
+
 template <int NR, int NC>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCtas))
     k_splat_warp(SceneDev sc, FrameDev fr, int *queue, float *out, int out_accum) {
@@ -462,6 +511,70 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 return;
             }
             const int cnt = min(kWStage, nrec - si * kWStage);
+            if constexpr (kRectDispatch<NR, NC>) {
+                // ---- decode the whole stage (kWStage / 32 records per lane), counting the
+                // records of each block rectangle
+                ws->cnt[lane] = 0;
+                __syncwarp();
+                int rid[kWStage / 32], rrank[kWStage / 32];
+#pragma unroll
+                for (int q = 0; q < kWStage / 32; ++q) {
+                    const int idx = q * 32 + lane;
+                    rid[q] = -1;
+                    rrank[q] = 0;
+                    if (idx < cnt) {
+                        const float4 rec = ws->buf[cb][idx];
+                        const float X = rec.x, Y = rec.y, R = rec.z;
+                        const uint32_t code = __float_as_uint(rec.w);
+                        const float eps = 1e-3f + 2e-6f * (fabsf(X) + fabsf(Y) + R);
+                        const int ilo = max(0, (int)ceilf(clampf(X - R - 0.5f - eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
+                        const int ihi = min(tw - 1, (int)floorf(clampf(X + R - 0.5f + eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
+                        const int jlo = max(0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))) - py0);
+                        const int jhi = min(th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))) - py0);
+                        if (ilo <= ihi && jlo <= jhi) {
+                            const int id = range_id(jlo >> 2, jhi >> 2, NR) * (NC * (NC + 1) / 2) +
+                                           range_id(ilo >> 3, ihi >> 3, NC);
+                            const int type = (int)(code >> 24);
+                            const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
+                            const int len = __ldg(&sc.lut_len[type]);
+                            const float f = It * (float)(len - 1);
+                            const int kk = min((int)f, len - 2);
+                            const float tau = f - (float)kk;
+                            const int lo = __ldg(&sc.lut_off[type]) + kk;
+                            const float4 c0 = __ldg(&sc.lut[lo]);
+                            const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                            const float R2 = __fmul_rn(R, R);
+                            float4 *d = reinterpret_cast<float4 *>(&ws->dec[idx]);
+                            d[0] = make_float4(X, Y, R2, __fdividef(kexp, R2));
+                            d[1] = make_float4((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
+                                               (1.0f - tau) * c0.z + tau * c1.z, 0.0f);
+                            rid[q] = id;
+                            rrank[q] = atomicAdd(&ws->cnt[id], 1);
+                        }
+                    }
+                }
+                __syncwarp();
+                // ---- group: exclusive scan of the per-rectangle counts (lane = rectangle)
+                const int c = ws->cnt[lane];
+                const int base = warp_incl_scan_i(c) - c;
+#pragma unroll
+                for (int q = 0; q < kWStage / 32; ++q) {
+                    const int b = __shfl_sync(0xffffffffu, base, rid[q] < 0 ? 0 : rid[q]);
+                    if (rid[q] >= 0) ws->ord[b + rrank[q]] = (unsigned char)(q * 32 + lane);
+                }
+                __syncwarp();
+                // ---- gather: one jump per rectangle present, then its records
+                uint32_t present = __ballot_sync(0xffffffffu, c > 0);
+                while (present) {
+                    const int id = __ffs(present) - 1;
+                    present &= present - 1;
+                    const int j0 = __shfl_sync(0xffffffffu, base, id);
+                    const int n = __shfl_sync(0xffffffffu, c, id);
+                    run_dispatch<NR, NC>(id, ws, j0, n, fx, fy, ar, ag, ab);
+                }
+                __syncwarp();
+                continue;
+            }
             for (int g = 0; g < cnt; g += 32) {
                 // ---- decode: one record per lane
                 uint32_t mask = 0;
