@@ -279,46 +279,48 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
 }
 
 // ---------------------------------------------------------------------------------------
-// Warp-per-item splat for tiles up to 24 px.  One warp owns every pixel of its item's tile
-// (NR x NC blocks of 8 x 4 pixels, all in registers), so the warps of a CTA never wait on
-// one another: in clustered data the density inside a tile is far from uniform, and with
-// the tile's pixel rows shared out among the CTA's warps the busiest warp set the pace.
-// Each warp stages its item's records by bulk copy into its own double buffer; each lane
-// decodes one record of a 32-record group (pixel box, block mask, colour, Gaussian
-// scale) into a small shared table, and the warp then walks the live records, evaluating
-// only the blocks the record's box overlaps.
+// Warp-per-item splat for tiles up to 32 px.  One warp owns every pixel of a square of at
+// most 16 x 16 pixels (NR x NC blocks of 8 x 4 pixels, all in registers): a tile of up
+// to 16 px, or one of the four quadrants of a larger tile, which are four separate work
+// items over the same record list (binning with the larger tile keeps the scatter's
+// open list slices within L2).  The warps of a CTA never wait on one another: in
+// clustered data the density inside a tile is far from uniform, and with a tile's pixel
+// rows shared out among several warps the busiest one set the pace.
+// Per stage of 128 records (bulk copy into the warp's own double buffer, mbarrier
+// completion with a bounded wait):
+//   1. each lane takes 4 records: pixel box inside the square, and the rectangle of
+//      blocks it covers; live records are counted per rectangle;
+//   2. the live records are grouped by rectangle (warp-local counting sort), and their
+//      colour (colormap) and Gaussian scale are computed, one record per lane;
+//   3. for every rectangle present, one jump to straight-line code for that rectangle,
+//      which runs over its records: each lane evaluates its pixel of every covered block
+//      with the FP32 coverage rule and adds e * w to its registers.
+// No atomics on pixels: a pixel has one owner.  Slices of a split tile add their partial
+// sums into a scratch tile and the last one to finish writes the tile.
 
 constexpr int kWarpsPerCta = 4;
 constexpr int kWStage = 128;  // records per bulk copy, per warp
 
 struct __align__(16) WRec {
     float X, Y, R2, kr;
-    float er, eg, eb;
-    uint32_t mask;  // blocks (r * NC + c) the record's box overlaps
+    float er, eg, eb, pad;
 };
 
 struct __align__(16) WarpSmem {
-    float4 buf[2][kWStage];
-    WRec dec[kWStage];          // decoded records of the stage
-    int cnt[32];                // records per block rectangle
-    unsigned char ord[kWStage]; // stage records grouped by block rectangle
+    float4 buf[2][kWStage];      // staged records
+    WRec dec[kWStage];           // decoded live records
+    int cnt[32];                 // live records per block rectangle
+    unsigned char ord[kWStage];  // live records grouped by rectangle
     uint64_t bar[2];
 };
 
 template <int NR, int NC>
 struct WarpShape {
-    static constexpr int kBlocks = NR * NC;
-    static_assert(kBlocks <= 32, "block mask is 32 bits");
-    // a 1 at the first block of every block row: multiplying an NC-bit column mask by it
-    // repeats the mask in every row
-    static constexpr uint64_t kRowRep = []() {
-        uint64_t r = 0;
-        for (int i = 0; i < NR; ++i) r |= 1ull << (i * NC);
-        return r;
-    }();
+    static constexpr int kRects = (NR * (NR + 1) / 2) * (NC * (NC + 1) / 2);
+    static_assert(kRects <= 32, "one lane per block rectangle");
     // resident CTAs per SM, which caps the registers: below about 80 per thread the
     // compiler reloads record fields from shared memory instead of keeping them
-    static constexpr int kMinCtas = kBlocks <= 2 ? 8 : (kBlocks <= 8 ? 6 : (kBlocks <= 18 ? 4 : 3));
+    static constexpr int kMinCtas = NR * NC <= 2 ? 8 : 6;
 };
 
 // Index of the block range [a, b] among the n (n + 1) / 2 ranges of n blocks.
@@ -346,43 +348,6 @@ __device__ __forceinline__ void rect_splat(const float (&fx)[NC], const float (&
         }
     }
 }
-
-// One indirect jump per record to the code of its block rectangle (tiles of 8 x 8 and
-// 16 x 16 pixels: 3 and 30 rectangles).
-#define SPL_RECT(R0, R1, C0, C1)                                                              \
-    case range_id(R0, R1, NR) * (NC * (NC + 1) / 2) + range_id(C0, C1, NC):                  \
-        rect_splat<NR, NC, R0, R1, C0, C1>(fx, fy, ar, ag, ab, pa, pb);                       \
-        break;
-#define SPL_ROWS4(C0, C1)                                                                      \
-    SPL_RECT(0, 0, C0, C1) SPL_RECT(0, 1, C0, C1) SPL_RECT(0, 2, C0, C1) SPL_RECT(0, 3, C0, C1) \
-    SPL_RECT(1, 1, C0, C1) SPL_RECT(1, 2, C0, C1) SPL_RECT(1, 3, C0, C1) SPL_RECT(2, 2, C0, C1) \
-    SPL_RECT(2, 3, C0, C1) SPL_RECT(3, 3, C0, C1)
-
-template <int NR, int NC>
-__device__ __forceinline__ void rect_dispatch(int id, const float (&fx)[NC], const float (&fy)[NR],
-                                              float (&ar)[NR][NC], float (&ag)[NR][NC], float (&ab)[NR][NC],
-                                              const float4 &pa, const float4 &pb) {
-    if constexpr (NR == 2 && NC == 1) {
-        switch (id) {
-            SPL_RECT(0, 0, 0, 0)
-            SPL_RECT(0, 1, 0, 0)
-            SPL_RECT(1, 1, 0, 0)
-            default: break;
-        }
-    } else if constexpr (NR == 4 && NC == 2) {
-        switch (id) {
-            SPL_ROWS4(0, 0)
-            SPL_ROWS4(0, 1)
-            SPL_ROWS4(1, 1)
-            default: break;
-        }
-    }
-}
-#undef SPL_ROWS4
-#undef SPL_RECT
-
-template <int NR, int NC>
-constexpr bool kRectDispatch = (NR == 2 && NC == 1) || (NR == 4 && NC == 2);
 
 // All records of one block rectangle, taken from the grouped order: the jump to the
 // rectangle's code is made once for the group.
@@ -420,7 +385,8 @@ __device__ __forceinline__ void run_dispatch(int id, const WarpSmem *ws, int j0,
             SPL_RUN(1, 1, 0, 0)
             default: break;
         }
-    } else if constexpr (NR == 4 && NC == 2) {
+    } else {
+        static_assert(NR == 4 && NC == 2, "shapes: 8 x 8 and 16 x 16 pixels");
         switch (id) {
             SPL_RUNS4(0, 0)
             SPL_RUNS4(0, 1)
@@ -434,18 +400,19 @@ __device__ __forceinline__ void run_dispatch(int id, const WarpSmem *ws, int j0,
 
 template <int NR, int NC>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCtas))
-    k_splat_warp(SceneDev sc, FrameDev fr, int *queue, float *out, int out_accum) {
-    using Shape = WarpShape<NR, NC>;
+    k_splat_warp(SceneDev sc, FrameDev fr, int *queue, float *out, int out_accum, int split) {
     if (fr.status[kStatOverflow]) return;
     extern __shared__ __align__(16) unsigned char s_raw[];
     WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_raw) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int nt = fr.n_tiles;
     const int N = fr.V * nt;
-    const int total_items = (int)fr.sizes[kSizeItems];
+    const int S2 = split * split;
+    const int total_items = (int)fr.sizes[kSizeItems] * S2;
     const int64_t K = fr.sizes[kSizeK];
     const ViewParams g0 = fr.views[0];
     const int T = g0.T, W = g0.W, H = g0.H, ntx = g0.ntx;
+    const int sub = (T + split - 1) / split;  // edge of the square a warp owns
     const int lc = lane & 7, lr = lane >> 3;
 
     if (lane == 0) {
@@ -462,22 +429,27 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total_items) break;
 
-        const int gt = find_tile(fr.item_off, N, item);
+        // item = (slice of a tile list, square of the tile); the squares of a slice are
+        // consecutive items, so they run at once and share the slice's records in L2
+        const int slice = item / S2, q = item - slice * S2;
+        const int gt = find_tile(fr.item_off, N, slice);
         const int v = gt / nt, t = gt - v * nt;
-        const int chunk = item - fr.item_off[gt];
-        const int n_it = fr.item_off[gt + 1] - fr.item_off[gt];
+        const int chunk = slice - fr.item_off[gt];
+        const int arrivals = (fr.item_off[gt + 1] - fr.item_off[gt]) * S2;
         const int slot = fr.split_slot[gt];
         const float kexp = fr.views[v].kexp;
         const int tx = t % ntx, ty = t / ntx;
-        const int px0 = tx * T, py0 = ty * T;
-        const int tw = min(T, W - px0), th = min(T, H - py0);
+        const int qx = (q % split) * sub, qy = (q / split) * sub;
+        const int px0 = tx * T + qx, py0 = ty * T + qy;
+        const int tw = max(0, min(min(sub, T - qx), W - px0));
+        const int th = max(0, min(min(sub, T - qy), H - py0));
         const int64_t seg1 = fr.offsets[gt + 1];
         const int64_t e0 = fr.offsets[gt] + (int64_t)chunk * K;
-        const int nrec = (int)(min(seg1, e0 + K) - e0);
+        const int nrec = (tw > 0 && th > 0) ? (int)(min(seg1, e0 + K) - e0) : 0;
         const int nst = (nrec + kWStage - 1) / kWStage;
 
-        // this lane's pixels: (c * 8 + lc, r * 4 + lr) of the tile; pixels outside the
-        // tile get a centre no support reaches
+        // this lane's pixels: (c * 8 + lc, r * 4 + lr) of the square; pixels outside it
+        // get a centre no support reaches
         float fx[NC], fy[NR], ar[NR][NC], ag[NR][NC], ab[NR][NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) fx[c] = c * 8 + lc < tw ? (float)(px0 + c * 8 + lc) + 0.5f : kFar;
@@ -511,78 +483,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 return;
             }
             const int cnt = min(kWStage, nrec - si * kWStage);
-            if constexpr (kRectDispatch<NR, NC>) {
-                // ---- decode the whole stage (kWStage / 32 records per lane), counting the
-                // records of each block rectangle
-                ws->cnt[lane] = 0;
-                __syncwarp();
-                int rid[kWStage / 32], rrank[kWStage / 32];
+            const float4 *recs = ws->buf[cb];
+
+            // ---- 1. pixel box and block rectangle of every record; count per rectangle
+            ws->cnt[lane] = 0;
+            __syncwarp();
+            int rid[kWStage / 32], rrank[kWStage / 32];
 #pragma unroll
-                for (int q = 0; q < kWStage / 32; ++q) {
-                    const int idx = q * 32 + lane;
-                    rid[q] = -1;
-                    rrank[q] = 0;
-                    if (idx < cnt) {
-                        const float4 rec = ws->buf[cb][idx];
-                        const float X = rec.x, Y = rec.y, R = rec.z;
-                        const uint32_t code = __float_as_uint(rec.w);
-                        const float eps = 1e-3f + 2e-6f * (fabsf(X) + fabsf(Y) + R);
-                        const int ilo = max(0, (int)ceilf(clampf(X - R - 0.5f - eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
-                        const int ihi = min(tw - 1, (int)floorf(clampf(X + R - 0.5f + eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
-                        const int jlo = max(0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))) - py0);
-                        const int jhi = min(th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))) - py0);
-                        if (ilo <= ihi && jlo <= jhi) {
-                            const int id = range_id(jlo >> 2, jhi >> 2, NR) * (NC * (NC + 1) / 2) +
-                                           range_id(ilo >> 3, ihi >> 3, NC);
-                            const int type = (int)(code >> 24);
-                            const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
-                            const int len = __ldg(&sc.lut_len[type]);
-                            const float f = It * (float)(len - 1);
-                            const int kk = min((int)f, len - 2);
-                            const float tau = f - (float)kk;
-                            const int lo = __ldg(&sc.lut_off[type]) + kk;
-                            const float4 c0 = __ldg(&sc.lut[lo]);
-                            const float4 c1 = __ldg(&sc.lut[lo + 1]);
-                            const float R2 = __fmul_rn(R, R);
-                            float4 *d = reinterpret_cast<float4 *>(&ws->dec[idx]);
-                            d[0] = make_float4(X, Y, R2, __fdividef(kexp, R2));
-                            d[1] = make_float4((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
-                                               (1.0f - tau) * c0.z + tau * c1.z, 0.0f);
-                            rid[q] = id;
-                            rrank[q] = atomicAdd(&ws->cnt[id], 1);
-                        }
-                    }
-                }
-                __syncwarp();
-                // ---- group: exclusive scan of the per-rectangle counts (lane = rectangle)
-                const int c = ws->cnt[lane];
-                const int base = warp_incl_scan_i(c) - c;
-#pragma unroll
-                for (int q = 0; q < kWStage / 32; ++q) {
-                    const int b = __shfl_sync(0xffffffffu, base, rid[q] < 0 ? 0 : rid[q]);
-                    if (rid[q] >= 0) ws->ord[b + rrank[q]] = (unsigned char)(q * 32 + lane);
-                }
-                __syncwarp();
-                // ---- gather: one jump per rectangle present, then its records
-                uint32_t present = __ballot_sync(0xffffffffu, c > 0);
-                while (present) {
-                    const int id = __ffs(present) - 1;
-                    present &= present - 1;
-                    const int j0 = __shfl_sync(0xffffffffu, base, id);
-                    const int n = __shfl_sync(0xffffffffu, c, id);
-                    run_dispatch<NR, NC>(id, ws, j0, n, fx, fy, ar, ag, ab);
-                }
-                __syncwarp();
-                continue;
-            }
-            for (int g = 0; g < cnt; g += 32) {
-                // ---- decode: one record per lane
-                uint32_t mask = 0;
-                if (g + lane < cnt) {
-                    const float4 rec = ws->buf[cb][g + lane];
+            for (int q4 = 0; q4 < kWStage / 32; ++q4) {
+                const int idx = q4 * 32 + lane;
+                rid[q4] = -1;
+                rrank[q4] = 0;
+                if (idx < cnt) {
+                    const float4 rec = recs[idx];
                     const float X = rec.x, Y = rec.y, R = rec.z;
-                    const uint32_t code = __float_as_uint(rec.w);
-                    // tight pixel range of the support inside the tile; eps exceeds the
+                    // tight pixel range of the support inside the square; eps exceeds the
                     // FP32 rounding of X +- R at any position, so no covered pixel is lost
                     const float eps = 1e-3f + 2e-6f * (fabsf(X) + fabsf(Y) + R);
                     const int ilo = max(0, (int)ceilf(clampf(X - R - 0.5f - eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
@@ -590,65 +505,57 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                     const int jlo = max(0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))) - py0);
                     const int jhi = min(th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))) - py0);
                     if (ilo <= ihi && jlo <= jhi) {
-                        if constexpr (kRectDispatch<NR, NC>) {
-                            mask = 1u + (uint32_t)(range_id(jlo >> 2, jhi >> 2, NR) * (NC * (NC + 1) / 2) +
-                                                   range_id(ilo >> 3, ihi >> 3, NC));
-                        } else {
-                            const uint32_t cm = (2u << (ihi >> 3)) - (1u << (ilo >> 3));
-                            const uint64_t rows =
-                                (1ull << (NC * ((jhi >> 2) + 1))) - (1ull << (NC * (jlo >> 2)));
-                            mask = (uint32_t)(rows & ((uint64_t)cm * Shape::kRowRep));
-                        }
-                        const int type = (int)(code >> 24);
-                        const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
-                        const int len = __ldg(&sc.lut_len[type]);
-                        const float f = It * (float)(len - 1);
-                        const int kk = min((int)f, len - 2);
-                        const float tau = f - (float)kk;
-                        const int lo = __ldg(&sc.lut_off[type]) + kk;
-                        const float4 c0 = __ldg(&sc.lut[lo]);
-                        const float4 c1 = __ldg(&sc.lut[lo + 1]);
-                        const float R2 = __fmul_rn(R, R);
-                        float4 *d = reinterpret_cast<float4 *>(&ws->dec[lane]);
-                        d[0] = make_float4(X, Y, R2, __fdividef(kexp, R2));
-                        d[1] = make_float4((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
-                                           (1.0f - tau) * c0.z + tau * c1.z, __uint_as_float(mask));
+                        const int id = range_id(jlo >> 2, jhi >> 2, NR) * (NC * (NC + 1) / 2) +
+                                       range_id(ilo >> 3, ihi >> 3, NC);
+                        rid[q4] = id;
+                        rrank[q4] = atomicAdd(&ws->cnt[id], 1);
                     }
                 }
-                uint32_t live = __ballot_sync(0xffffffffu, mask != 0);
-                __syncwarp();
-                // ---- gather: every live record over the blocks its box overlaps
-                while (live) {
-                    const int k = __ffs(live) - 1;
-                    live &= live - 1;
-                    const float4 pa = *reinterpret_cast<const float4 *>(&ws->dec[k].X);
-                    const float4 pb = *reinterpret_cast<const float4 *>(&ws->dec[k].er);
-                    const uint32_t m = __float_as_uint(pb.w);
-                    if constexpr (kRectDispatch<NR, NC>) {
-                        rect_dispatch<NR, NC>((int)m - 1, fx, fy, ar, ag, ab, pa, pb);
-                    } else {
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        if (!(m & (((1u << NC) - 1u) << (r * NC)))) continue;
-                        const float dy = __fsub_rn(fy[r], pa.y);
-                        const float dy2 = __fmul_rn(dy, dy);
-#pragma unroll
-                        for (int c = 0; c < NC; ++c) {
-                            if (!(m & (1u << (r * NC + c)))) continue;
-                            const float dx = __fsub_rn(fx[c], pa.x);
-                            const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2);
-                            if (d2 < pa.z) {
-                                const float w = ex2_fast(d2 * pa.w);
-                                ar[r][c] += pb.x * w;
-                                ag[r][c] += pb.y * w;
-                                ab[r][c] += pb.z * w;
-                            }
-                        }
-                    }
-                    }
-                }
-                __syncwarp();
             }
+            __syncwarp();
+            // ---- 2. group the live records by rectangle (lane = rectangle)
+            const int c = ws->cnt[lane];
+            const int incl = warp_incl_scan_i(c);
+            const int base = incl - c;
+            const int nlive = __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+            for (int q4 = 0; q4 < kWStage / 32; ++q4) {
+                const int b = __shfl_sync(0xffffffffu, base, rid[q4] < 0 ? 0 : rid[q4]);
+                if (rid[q4] >= 0) ws->ord[b + rrank[q4]] = (unsigned char)(q4 * 32 + lane);
+            }
+            __syncwarp();
+            // colour and Gaussian scale of the live records only, one per lane
+            for (int j = lane; j < nlive; j += 32) {
+                const int k = ws->ord[j];
+                const float4 rec = recs[k];
+                const float R = rec.z;
+                const uint32_t code = __float_as_uint(rec.w);
+                const int type = (int)(code >> 24);
+                const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
+                const int len = __ldg(&sc.lut_len[type]);
+                const float f = It * (float)(len - 1);
+                const int kk = min((int)f, len - 2);
+                const float tau = f - (float)kk;
+                const int lo = __ldg(&sc.lut_off[type]) + kk;
+                const float4 c0 = __ldg(&sc.lut[lo]);
+                const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                const float R2 = __fmul_rn(R, R);
+                float4 *d = reinterpret_cast<float4 *>(&ws->dec[k]);
+                d[0] = make_float4(rec.x, rec.y, R2, __fdividef(kexp, R2));
+                d[1] = make_float4((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
+                                   (1.0f - tau) * c0.z + tau * c1.z, 0.0f);
+            }
+            __syncwarp();
+            // ---- 3. one jump per rectangle present, then its records
+            uint32_t present = __ballot_sync(0xffffffffu, c > 0);
+            while (present) {
+                const int id = __ffs(present) - 1;
+                present &= present - 1;
+                const int j0 = __shfl_sync(0xffffffffu, base, id);
+                const int n = __shfl_sync(0xffffffffu, c, id);
+                run_dispatch<NR, NC>(id, ws, j0, n, fx, fy, ar, ag, ab);
+            }
+            __syncwarp();
         }
 
         // epilogue: final transform of this lane's pixels, or merge of a split tile
@@ -658,12 +565,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
             for (int r = 0; r < NR; ++r) {
                 if (r * 4 + lr >= th) continue;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    if (c * 8 + lc >= tw) continue;
-                    float *p = o + ((int64_t)(py0 + r * 4 + lr) * W + px0 + c * 8 + lc) * 3;
-                    p[0] = out_accum ? ar[r][c] : -expm1f(-ar[r][c]);
-                    p[1] = out_accum ? ag[r][c] : -expm1f(-ag[r][c]);
-                    p[2] = out_accum ? ab[r][c] : -expm1f(-ab[r][c]);
+                for (int cc = 0; cc < NC; ++cc) {
+                    if (cc * 8 + lc >= tw) continue;
+                    float *p = o + ((int64_t)(py0 + r * 4 + lr) * W + px0 + cc * 8 + lc) * 3;
+                    p[0] = out_accum ? ar[r][cc] : -expm1f(-ar[r][cc]);
+                    p[1] = out_accum ? ag[r][cc] : -expm1f(-ag[r][cc]);
+                    p[2] = out_accum ? ab[r][cc] : -expm1f(-ab[r][cc]);
                 }
             }
         } else {
@@ -672,27 +579,30 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
             for (int r = 0; r < NR; ++r) {
                 if (r * 4 + lr >= th) continue;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    if (c * 8 + lc >= tw) continue;
-                    const int pix = (r * 4 + lr) * T + c * 8 + lc;
-                    if (ar[r][c] != 0.0f) atomicAdd(&scr[pix], ar[r][c]);
-                    if (ag[r][c] != 0.0f) atomicAdd(&scr[T * T + pix], ag[r][c]);
-                    if (ab[r][c] != 0.0f) atomicAdd(&scr[2 * T * T + pix], ab[r][c]);
+                for (int cc = 0; cc < NC; ++cc) {
+                    if (cc * 8 + lc >= tw) continue;
+                    const int pix = (qy + r * 4 + lr) * T + qx + cc * 8 + lc;
+                    if (ar[r][cc] != 0.0f) atomicAdd(&scr[pix], ar[r][cc]);
+                    if (ag[r][cc] != 0.0f) atomicAdd(&scr[T * T + pix], ag[r][cc]);
+                    if (ab[r][cc] != 0.0f) atomicAdd(&scr[2 * T * T + pix], ab[r][cc]);
                 }
             }
             __threadfence();
             __syncwarp();
             int last = 0;
-            if (lane == 0) last = (atomicAdd(&fr.tickets[slot], 1) == n_it - 1);
+            if (lane == 0) last = (atomicAdd(&fr.tickets[slot], 1) == arrivals - 1);
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
+                // the whole tile, from the scratch every square of every slice added into
                 __threadfence();
-                const int rowlen = 3 * tw;
-                for (int k = lane; k < th * rowlen; k += 32) {
-                    const int rr = k / rowlen, cc = k - rr * rowlen;
-                    const int col = cc / 3, ch = cc - col * 3;
+                const int TW = min(T, W - tx * T), TH = min(T, H - ty * T);
+                const int rowlen = 3 * TW;
+                float *ot = o + ((int64_t)ty * T * W + (int64_t)tx * T) * 3;
+                for (int k = lane; k < TH * rowlen; k += 32) {
+                    const int rr = k / rowlen, c3 = k - rr * rowlen;
+                    const int col = c3 / 3, ch = c3 - col * 3;
                     const float a = __ldcg(&scr[ch * T * T + rr * T + col]);
-                    o[((int64_t)(py0 + rr) * W + px0) * 3 + cc] = out_accum ? a : -expm1f(-a);
+                    ot[(int64_t)rr * W * 3 + c3] = out_accum ? a : -expm1f(-a);
                 }
                 __syncwarp();
                 for (int k = lane; k < 3 * T * T; k += 32) scr[k] = 0.0f;
@@ -704,22 +614,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
 }
 
 typedef void (*SplatFn)(SceneDev, FrameDev, int *, float *, int);
+typedef void (*WarpSplatFn)(SceneDev, FrameDev, int *, float *, int, int);
 
-// tiles up to kWarpTileMax px: warp per item; larger tiles: CTA per item
-constexpr int kWarpTileMax = 24;
+// Tiles up to 32 px: warp per square of up to 16 px (a tile above 16 px is split into
+// four squares); larger tiles: CTA per item.
+constexpr int kWarpTileMax = 32;
 static bool warp_kernel(int T) { return T <= kWarpTileMax; }
+int splat_split(int T) { return T > 16 && warp_kernel(T) ? 2 : 1; }
 
-static SplatFn splat_fn(int T) {
-    if (warp_kernel(T)) {
-        if (T <= 8) return k_splat_warp<2, 1>;
-        if (T <= 16) return k_splat_warp<4, 2>;
-        return k_splat_warp<6, 3>;
-    }
+static WarpSplatFn warp_fn(int T) { return T <= 8 ? k_splat_warp<2, 1> : k_splat_warp<4, 2>; }
+
+static SplatFn cta_fn(int T) {
     switch (block_cols(T)) {
-        case 1: return k_splat<1, 1>;
-        case 2: return k_splat<1, 2>;
-        case 3: return k_splat<1, 3>;
-        case 4: return k_splat<1, 4>;
         case 5: return k_splat<2, 5>;
         case 6: return k_splat<2, 6>;
         case 7: return k_splat<2, 7>;
@@ -727,13 +633,15 @@ static SplatFn splat_fn(int T) {
     }
 }
 
+static const void *splat_kernel(int T) { return warp_kernel(T) ? (const void *)warp_fn(T) : (const void *)cta_fn(T); }
+
 static size_t splat_smem(int T) { return warp_kernel(T) ? sizeof(WarpSmem) * kWarpsPerCta : splat_smem_bytes(T); }
 static int splat_cta_threads(int T) { return warp_kernel(T) ? kWarpsPerCta * 32 : kSplatThreads; }
 
 int splat_blocks_per_sm(int T) {
     const size_t smem = splat_smem(T);
-    SplatFn fn = splat_fn(T);
-    if (ensure_smem_limit((const void *)fn, smem) != cudaSuccess) return 0;
+    const void *fn = splat_kernel(T);
+    if (ensure_smem_limit(fn, smem) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, splat_cta_threads(T), smem) != cudaSuccess) return 0;
     return nb;
@@ -744,10 +652,12 @@ int splat_workers_per_sm(int T) { return splat_blocks_per_sm(T) * (warp_kernel(T
 cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, float *out, int out_accum,
                          int grid, cudaStream_t st) {
     const size_t smem = splat_smem(fr.T);
-    SplatFn fn = splat_fn(fr.T);
-    cudaError_t err = ensure_smem_limit((const void *)fn, smem);
+    cudaError_t err = ensure_smem_limit(splat_kernel(fr.T), smem);
     if (err != cudaSuccess) return err;
-    fn<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum);
+    if (warp_kernel(fr.T))
+        warp_fn(fr.T)<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum, splat_split(fr.T));
+    else
+        cta_fn(fr.T)<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum);
     return cudaGetLastError();
 }
 

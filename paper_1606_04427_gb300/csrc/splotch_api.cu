@@ -616,14 +616,20 @@ static FrameDev frame_dev(const FrameHost &fh, char *fixed, char *var) {
     return fr;
 }
 
+// items: work items of the scan (tile-list slices); the splat renders each as split^2
+// squares, one worker each
 static int splat_grid(int dev, int T, int items) {
     const int bps = std::max(1, splat_blocks_per_sm(T));
     const int per_cta = std::max(1, splat_workers_per_sm(T) / bps);
     const int g = sm_count(dev) * bps;
-    return std::max(1, std::min(g, (std::max(1, items) + per_cta - 1) / per_cta));
+    const int64_t squares = (int64_t)std::max(1, items) * splat_split(T) * splat_split(T);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (squares + per_cta - 1) / per_cta));
 }
 
-static int target_items(int dev, int T) { return sm_count(dev) * std::max(1, splat_workers_per_sm(T)) * 4; }
+static int target_items(int dev, int T) {
+    const int s = splat_split(T);
+    return std::max(1, sm_count(dev) * std::max(1, splat_workers_per_sm(T)) * 4 / (s * s));
+}
 static const int kMinItemPairs = 2048;
 
 struct RenderSetup {

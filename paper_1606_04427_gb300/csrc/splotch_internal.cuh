@@ -281,6 +281,7 @@ cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, flo
                          int out_accum, int grid, cudaStream_t st);
 int splat_blocks_per_sm(int T);
 int splat_workers_per_sm(int T);
+int splat_split(int T);  // squares per tile edge the splat renders separately (1 or 2)
 int bin_ctas_per_sm(int storage, size_t smem);
 
 // Raise a kernel's dynamic shared-memory limit on the current device to at least
