@@ -19,7 +19,7 @@ namespace spl {
 constexpr int kMaxTiles = 16384;   // tiles per image (per-CTA shared histogram)
 constexpr int kMaxTile = 64;       // tile edge in pixels (shared accumulator)
 constexpr int kMaxTypes = 255;     // species (8-bit type field in the tile records)
-constexpr int kThreads = 256;      // CTA size of the particle-stream kernels
+constexpr int kThreads = 1024;     // CTA size of the particle-stream kernels (one per SM: one tile histogram per SM)
 constexpr int kSplatThreads = 256; // CTA size of the splat kernel
 constexpr int kSplatWarps = kSplatThreads / 32;
 constexpr int kStage = 512;        // tile records per bulk-copy stage
