@@ -332,14 +332,20 @@ template <int NR, int NC, int R0, int R1, int C0, int C1>
 __device__ __forceinline__ void rect_splat(const float (&fx)[NC], const float (&fy)[NR], float (&ar)[NR][NC],
                                            float (&ag)[NR][NC], float (&ab)[NR][NC], const float4 &pa,
                                            const float4 &pb) {
+    // dx^2 once per block column, dy^2 once per block row (same rounding as per pixel)
+    float dx2[NC];
+#pragma unroll
+    for (int c = C0; c <= C1; ++c) {
+        const float dx = __fsub_rn(fx[c], pa.x);
+        dx2[c] = __fmul_rn(dx, dx);
+    }
 #pragma unroll
     for (int r = R0; r <= R1; ++r) {
         const float dy = __fsub_rn(fy[r], pa.y);
         const float dy2 = __fmul_rn(dy, dy);
 #pragma unroll
         for (int c = C0; c <= C1; ++c) {
-            const float dx = __fsub_rn(fx[c], pa.x);
-            const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2);
+            const float d2 = __fadd_rn(dx2[c], dy2);
             float w = ex2_fast(d2 * pa.w);
             w = d2 < pa.z ? w : 0.0f;
             ar[r][c] += pb.x * w;
