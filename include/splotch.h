@@ -72,7 +72,9 @@ typedef struct {
  *   n_types      1..255
  *   type_begin   host, n_types + 1 entries, type_begin[0] = 0, non-decreasing, last = n
  *   x y z h intensity   n floats each (FP32), on the device when on_device != 0, else host;
- *                h > 0 (smoothing length, world units); all finite
+ *                h > 0 (smoothing length, world units); all finite.  Host inputs that
+ *                are all page-locked (cudaHostAlloc / cudaHostRegister) are read in place
+ *                by the device; pageable host inputs are first copied to device staging
  *   storage      splotch_storage for the resident copy of x, y, z, h and the normalised
  *                intensity (FP16 / BF16 round to nearest even from FP32)
  *   cmap_rgb     host, per type a pointer to cmap_len[t] RGB triples (FP32), cmap_len >= 2

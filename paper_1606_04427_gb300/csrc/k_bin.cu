@@ -88,8 +88,8 @@ __global__ void k_prepare(const float *__restrict__ x, const float *__restrict__
                           const float *__restrict__ I, int64_t n, int n_types,
                           const int64_t *__restrict__ tb, const float *__restrict__ lo,
                           const float *__restrict__ hi, const int *__restrict__ i_log, T *ox, T *oy,
-                          T *oz, T *oh, T *oit, int *bad) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+                          T *oz, T *oh, T *oit, int *bad, int64_t first) {
+    for (int64_t i = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int a = 0, b = n_types - 1;  // species: last t with tb[t] <= i
         while (a < b) {
@@ -111,29 +111,87 @@ __global__ void k_prepare(const float *__restrict__ x, const float *__restrict__
     }
 }
 
+// Four consecutive particles per thread with 16-byte loads of every input array (inputs
+// 16-byte aligned): a quarter of the memory requests, which matters when the inputs are
+// read in place from page-locked host memory over the host link.
+template <typename T>
+__global__ void k_prepare4(const float4 *__restrict__ x, const float4 *__restrict__ y,
+                           const float4 *__restrict__ z, const float4 *__restrict__ h,
+                           const float4 *__restrict__ I, int64_t n4, int n_types,
+                           const int64_t *__restrict__ tb, const float *__restrict__ lo,
+                           const float *__restrict__ hi, const int *__restrict__ i_log, T *ox, T *oy,
+                           T *oz, T *oh, T *oit, int *bad) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+        const float4 xv = x[q], yv = y[q], zv = z[q], hv = h[q], Iv = I[q];
+        const float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ys[4] = {yv.x, yv.y, yv.z, yv.w};
+        const float zs[4] = {zv.x, zv.y, zv.z, zv.w}, hs[4] = {hv.x, hv.y, hv.z, hv.w};
+        const float is[4] = {Iv.x, Iv.y, Iv.z, Iv.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = 4 * q + k;
+            int a = 0, b = n_types - 1;  // species: last t with tb[t] <= i
+            while (a < b) {
+                int mid = (a + b + 1) >> 1;
+                if (tb[mid] <= i) a = mid; else b = mid - 1;
+            }
+            if (!(isfinite(xs[k]) && isfinite(ys[k]) && isfinite(zs[k]) && isfinite(hs[k]) && hs[k] > 0.0f &&
+                  isfinite(is[k])))
+                atomicOr(bad, 1);
+            float v = i_log[a] ? logf(fmaxf(is[k], 1e-30f)) : is[k];
+            const float span = __fsub_rn(hi[a], lo[a]);
+            float t = span > 0.0f ? __fdiv_rn(__fsub_rn(v, lo[a]), span) : 0.0f;
+            t = fminf(fmaxf(t, 0.0f), 1.0f);
+            ox[i] = to_store<T>(xs[k]);
+            oy[i] = to_store<T>(ys[k]);
+            oz[i] = to_store<T>(zs[k]);
+            oh[i] = to_store<T>(hs[k]);
+            oit[i] = to_store<T>(t);
+        }
+    }
+}
+
+template <typename T>
+static void prepare_launch(const float *x, const float *y, const float *z, const float *h, const float *I,
+                           int64_t n, int n_types, const int64_t *tb, const float *lo, const float *hi,
+                           const int *i_log, void *ox, void *oy, void *oz, void *oh, void *oit, int *bad,
+                           cudaStream_t st) {
+    auto aligned = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+    int64_t done = 0;
+    if (aligned(x) && aligned(y) && aligned(z) && aligned(h) && aligned(I) && n >= 4) {
+        const int64_t n4 = n / 4;
+        int64_t blocks = (n4 + 255) / 256;
+        if (blocks > 65536) blocks = 65536;
+        k_prepare4<T><<<(int)blocks, 256, 0, st>>>((const float4 *)x, (const float4 *)y, (const float4 *)z,
+                                                   (const float4 *)h, (const float4 *)I, n4, n_types, tb, lo, hi,
+                                                   i_log, (T *)ox, (T *)oy, (T *)oz, (T *)oh, (T *)oit, bad);
+        done = 4 * n4;
+    }
+    if (done < n) {
+        // the remaining particles (or all, for unaligned inputs), one per thread; the
+        // outputs are offset so indices stay global
+        int64_t blocks = (n - done + 255) / 256;
+        if (blocks > 65536) blocks = 65536;
+        k_prepare<T><<<(int)blocks, 256, 0, st>>>(x, y, z, h, I, n, n_types, tb, lo, hi, i_log, (T *)ox, (T *)oy,
+                                                  (T *)oz, (T *)oh, (T *)oit, bad, done);
+    }
+}
+
 cudaError_t launch_prepare(const float *x, const float *y, const float *z, const float *h,
                            const float *I, int64_t n, int n_types, const int64_t *type_begin,
                            const float *lo, const float *hi, const int *i_log, int storage,
                            void *ox, void *oy, void *oz, void *oh, void *oit, int *bad,
                            cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 65536) blocks = 65536;
     switch (storage) {
     case 0:
-        k_prepare<float><<<(int)blocks, 256, 0, st>>>(x, y, z, h, I, n, n_types, type_begin, lo, hi, i_log,
-                                                      (float *)ox, (float *)oy, (float *)oz, (float *)oh,
-                                                      (float *)oit, bad);
+        prepare_launch<float>(x, y, z, h, I, n, n_types, type_begin, lo, hi, i_log, ox, oy, oz, oh, oit, bad, st);
         break;
     case 1:
-        k_prepare<__half><<<(int)blocks, 256, 0, st>>>(x, y, z, h, I, n, n_types, type_begin, lo, hi, i_log,
-                                                       (__half *)ox, (__half *)oy, (__half *)oz,
-                                                       (__half *)oh, (__half *)oit, bad);
+        prepare_launch<__half>(x, y, z, h, I, n, n_types, type_begin, lo, hi, i_log, ox, oy, oz, oh, oit, bad, st);
         break;
     default:
-        k_prepare<__nv_bfloat16><<<(int)blocks, 256, 0, st>>>(
-            x, y, z, h, I, n, n_types, type_begin, lo, hi, i_log, (__nv_bfloat16 *)ox,
-            (__nv_bfloat16 *)oy, (__nv_bfloat16 *)oz, (__nv_bfloat16 *)oh, (__nv_bfloat16 *)oit, bad);
+        prepare_launch<__nv_bfloat16>(x, y, z, h, I, n, n_types, type_begin, lo, hi, i_log, ox, oy, oz, oh, oit,
+                                      bad, st);
     }
     return cudaGetLastError();
 }

@@ -304,29 +304,52 @@ extern "C" splotch_status splotch_create_scene(const splotch_scene_desc *d, splo
     cudaMemcpyAsync(mb + o_len, lut_len.data(), sizeof(int) * d->n_types, cudaMemcpyHostToDevice, st);
 
     char *ab = (char *)sc->attr;
-    if (cudaMemsetAsync(ab, 0, sc->attr_bytes, st) != cudaSuccess)
-        return cleanup(fail(SPLOTCH_ERR_CUDA, "memset scene"));
+    // the preparation kernel writes [0, n) of every array; zero the padding behind it
+    for (int k = 0; k < 5; ++k)
+        if (cudaMemsetAsync(ab + k * arr + (size_t)d->n * elem, 0, arr - (size_t)d->n * elem, st) != cudaSuccess)
+            return cleanup(fail(SPLOTCH_ERR_CUDA, "memset scene"));
 
     if (d->n > 0) {
-        // staging: FP32 inputs on the device, per-type range, validity flag
+        // Host inputs in page-locked memory are read by the preparation kernel in place
+        // (through their device-visible address: no staging copy); pageable host inputs
+        // are staged on the device first.
+        const float *src[5] = {d->x, d->y, d->z, d->h, d->intensity};
+        const float *in[5];
+        bool copy_in = !d->on_device;
+        if (copy_in) {
+            bool pinned = true;
+            for (int k = 0; k < 5 && pinned; ++k) {
+                cudaPointerAttributes pa{};
+                if (cudaPointerGetAttributes(&pa, src[k]) != cudaSuccess) {
+                    cudaGetLastError();
+                    pinned = false;
+                } else if (pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
+                    pinned = false;
+                } else {
+                    in[k] = (const float *)pa.devicePointer;
+                }
+            }
+            copy_in = !pinned;
+        }
+        // staging: FP32 inputs on the device (pageable host inputs only), per-type range,
+        // validity flag
         Carve sv;
         const size_t f = sizeof(float) * (size_t)d->n;
-        const size_t o_in[5] = {sv.take(f), sv.take(f), sv.take(f), sv.take(f), sv.take(f)};
+        size_t o_in[5] = {0, 0, 0, 0, 0};
+        if (copy_in)
+            for (int k = 0; k < 5; ++k) o_in[k] = sv.take(f);
         const size_t o_lo = sv.take(sizeof(float) * d->n_types);
         const size_t o_hi = sv.take(sizeof(float) * d->n_types);
         const size_t o_lg = sv.take(sizeof(int) * d->n_types);
         const size_t o_keys = sv.take(sizeof(unsigned) * 2 * d->n_types);
         const size_t o_bad = sv.take(sizeof(int));
-        const bool copy_in = !d->on_device;
         char *stg = (char *)sc->mem.alloc(sv.off, st);
         if (!stg) return cleanup(fail(SPLOTCH_ERR_OOM, "scene staging"));
-        const float *src[5] = {d->x, d->y, d->z, d->h, d->intensity};
-        const float *in[5];
         for (int k = 0; k < 5; ++k) {
             if (copy_in) {
                 cudaMemcpyAsync(stg + o_in[k], src[k], f, cudaMemcpyHostToDevice, st);
                 in[k] = (const float *)(stg + o_in[k]);
-            } else {
+            } else if (d->on_device) {
                 in[k] = src[k];
             }
         }
