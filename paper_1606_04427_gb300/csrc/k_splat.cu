@@ -308,7 +308,7 @@ struct __align__(16) WRec {
 
 struct __align__(16) WarpSmem {
     float4 buf[2][kWStage];      // staged records
-    WRec dec[kWStage];           // decoded live records
+    WRec dec[kWStage];           // decoded live records, grouped by rectangle
     int cnt[32];                 // live records per block rectangle
     unsigned char ord[kWStage];  // live records grouped by rectangle
     uint64_t bar[2];
@@ -346,11 +346,15 @@ __device__ __forceinline__ void rect_splat(const float (&fx)[NC], const float (&
 #pragma unroll
         for (int c = C0; c <= C1; ++c) {
             const float d2 = __fadd_rn(dx2[c], dy2);
-            float w = ex2_fast(d2 * pa.w);
-            w = d2 < pa.z ? w : 0.0f;
-            ar[r][c] += pb.x * w;
-            ag[r][c] += pb.y * w;
-            ab[r][c] += pb.z * w;
+            const float w = ex2_fast(d2 * pa.w);
+            // a += e * w only where d2 < R^2 (predicated: uncovered pixels add nothing)
+            asm("{\n\t.reg .pred p;\n\t"
+                "setp.lt.f32 p, %3, %4;\n\t"
+                "@p fma.rn.f32 %0, %5, %8, %0;\n\t"
+                "@p fma.rn.f32 %1, %6, %8, %1;\n\t"
+                "@p fma.rn.f32 %2, %7, %8, %2;\n\t}"
+                : "+f"(ar[r][c]), "+f"(ag[r][c]), "+f"(ab[r][c])
+                : "f"(d2), "f"(pa.z), "f"(pb.x), "f"(pb.y), "f"(pb.z), "f"(w));
         }
     }
 }
@@ -364,9 +368,8 @@ __device__ __forceinline__ void rect_run(const WarpSmem *ws, int j0, int n, cons
     // not unrolled: 30 copies of an unrolled loop overflow the instruction cache
 #pragma unroll 1
     for (int j = j0; j < j0 + n; ++j) {
-        const int k = ws->ord[j];
-        const float4 pa = *reinterpret_cast<const float4 *>(&ws->dec[k].X);
-        const float4 pb = *reinterpret_cast<const float4 *>(&ws->dec[k].er);
+        const float4 pa = *reinterpret_cast<const float4 *>(&ws->dec[j].X);
+        const float4 pb = *reinterpret_cast<const float4 *>(&ws->dec[j].er);
         rect_splat<NR, NC, R0, R1, C0, C1>(fx, fy, ar, ag, ab, pa, pb);
     }
 }
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 const float4 c0 = __ldg(&sc.lut[lo]);
                 const float4 c1 = __ldg(&sc.lut[lo + 1]);
                 const float R2 = __fmul_rn(R, R);
-                float4 *d = reinterpret_cast<float4 *>(&ws->dec[k]);
+                float4 *d = reinterpret_cast<float4 *>(&ws->dec[j]);  // in grouped order
                 d[0] = make_float4(rec.x, rec.y, R2, __fdividef(kexp, R2));
                 d[1] = make_float4((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
                                    (1.0f - tau) * c0.z + tau * c1.z, 0.0f);
