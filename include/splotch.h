@@ -127,6 +127,9 @@ typedef struct {
  *                 rounded up to a multiple of 1024 (FP32) or 2048 (FP16 / BF16);
  *                 0 = about four CTAs per SM.  A tuning knob with no effect on results.
  *   flags         SPLOTCH_OUT_ACCUM: write the accumulation a instead of 1 - exp(-a);
+ *                 SPLOTCH_OUT_ADD: add the accumulation a to what `out` holds (several
+ *                 renders, e.g. particle subsets, summed in one image; the final transform
+ *                 is then applied once with splotch_final_transform);
  *                 SPLOTCH_SYNC: splotch_render waits for the frame and reports a device-side
  *                 TIMEOUT before returning; SPLOTCH_PLAN_GRAPH: a plan captures its launch
  *                 sequence into a CUDA graph on first launch and replays it afterwards;
@@ -142,7 +145,7 @@ typedef struct {
     int32_t flags;
 } splotch_render_params;
 
-enum { SPLOTCH_OUT_ACCUM = 1, SPLOTCH_SYNC = 2, SPLOTCH_PLAN_GRAPH = 4, SPLOTCH_TIMING = 8 };
+enum { SPLOTCH_OUT_ACCUM = 1, SPLOTCH_SYNC = 2, SPLOTCH_PLAN_GRAPH = 4, SPLOTCH_TIMING = 8, SPLOTCH_OUT_ADD = 16 };
 
 /* Defaults listed above. */
 splotch_render_params splotch_default_params(void);
@@ -180,6 +183,21 @@ splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], flo
  * reaches that point.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA, TIMEOUT. */
 splotch_status splotch_render(splotch_scene *scene, const splotch_camera *cams, int32_t n_views,
                               const splotch_render_params *params, float *out, void *stream);
+
+/* Out-of-core render of one view (Section 3.2: data larger than the accelerator's memory is
+ * processed in pieces).  The particle set `desc` stays where it is (host or device, as for
+ * splotch_create_scene) and is rendered in chunks of at most `chunk` particles: each chunk
+ * is prepared on the device (page-locked host inputs read in place) on a side stream while
+ * the previous chunk renders on `stream`, and its accumulation is added to `out`.  With
+ * absorption = emission the accumulation is a sum over particles, so the result equals
+ * splotch_render of the whole set up to FP32 summation order.  Intensity ranges not given
+ * are computed exactly over the whole set first (one extra pass over the intensities).
+ * Flags: SPLOTCH_OUT_ACCUM leaves the accumulation a in `out`; SPLOTCH_OUT_ADD adds it to
+ * what `out` holds; otherwise `out` = 1 - exp(-a).  Device memory: two chunks' resident
+ * attributes plus one chunk's frame workspace.  Synchronous: returns when `out` is ready.
+ * Errors: as splotch_create_scene and splotch_render; INVALID_ARG if chunk < 1. */
+splotch_status splotch_render_streamed(const splotch_scene_desc *desc, int64_t chunk, const splotch_camera *cam,
+                                       const splotch_render_params *params, float *out, void *stream);
 
 /* Final transform in place: a[k] <- 1 - exp(-a[k]) for k < count (device FP32 buffer).
  * With SPLOTCH_OUT_ACCUM renders this finishes an accumulation image, e.g. after the

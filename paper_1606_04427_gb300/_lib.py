@@ -15,7 +15,7 @@ from . import build as _build
 OK, INVALID_ARG, OOM, CUDA, CAPACITY, TIMEOUT, UNSUPPORTED = range(7)
 F32, F16, BF16 = 0, 1, 2
 STORAGE = {"f32": F32, "f16": F16, "bf16": BF16}
-OUT_ACCUM, SYNC, PLAN_GRAPH, TIMING = 1, 2, 4, 8
+OUT_ACCUM, SYNC, PLAN_GRAPH, TIMING, OUT_ADD = 1, 2, 4, 8, 16
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -79,6 +79,8 @@ SIGNATURES = {
     "splotch_selftest_bounded_wait": ([C.c_int64, C.c_void_p], C.c_int),
     "splotch_final_transform": ([C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "splotch_last_timing": ([C.c_void_p, C.c_void_p], C.c_int),
+    "splotch_render_streamed": ([C.POINTER(SceneDesc), C.c_int64, C.POINTER(CameraC), C.POINTER(RenderParamsC),
+                                 C.c_void_p, C.c_void_p], C.c_int),
     "splotch_render_noalloc": ([C.c_void_p, C.POINTER(CameraC), C.POINTER(RenderParamsC), C.c_void_p,
                                 C.c_void_p], C.c_int),
     "splotch_status_string": ([C.c_int], C.c_char_p),

@@ -56,6 +56,12 @@ size_t splat_smem_bytes(int) {
 // pixel centre coordinate that no support reaches (its square overflows to +inf)
 constexpr float kFar = 1e30f;
 
+// Output of a pixel's accumulation a: mode 0 writes 1 - exp(-a) (final transform),
+// 1 writes a, 2 adds a to what the pixel holds (several renders summed in one image).
+__device__ __forceinline__ void put_pixel(float *p, float a, int mode) {
+    *p = mode == 2 ? *p + a : (mode ? a : -expm1f(-a));
+}
+
 template <int NR, int NC>
 __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDev fr, int *queue, float *out,
                                                          int out_accum) {
@@ -236,9 +242,9 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 for (int c = 0; c < NC; ++c) {
                     if (c * 8 + lc >= tw) continue;
                     float *p = o + ((int64_t)(py0 + row) * W + px0 + c * 8 + lc) * 3;
-                    p[0] = out_accum ? ar[rr][c] : -expm1f(-ar[rr][c]);
-                    p[1] = out_accum ? ag[rr][c] : -expm1f(-ag[rr][c]);
-                    p[2] = out_accum ? ab[rr][c] : -expm1f(-ab[rr][c]);
+                    put_pixel(p, ar[rr][c], out_accum);
+                    put_pixel(p + 1, ag[rr][c], out_accum);
+                    put_pixel(p + 2, ab[rr][c], out_accum);
                 }
             }
         } else {
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                     const int r = k / rowlen, cc = k - r * rowlen;
                     const int col = cc / 3, ch = cc - col * 3;
                     const float a = __ldcg(&scr[ch * T * T + r * T + col]);
-                    o[((int64_t)(py0 + r) * W + px0) * 3 + cc] = out_accum ? a : -expm1f(-a);
+                    put_pixel(&o[((int64_t)(py0 + r) * W + px0) * 3 + cc], a, out_accum);
                 }
                 __syncthreads();
                 for (int k = tid; k < 3 * T * T; k += kSplatThreads) scr[k] = 0.0f;
@@ -577,9 +583,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 for (int cc = 0; cc < NC; ++cc) {
                     if (cc * 8 + lc >= tw) continue;
                     float *p = o + ((int64_t)(py0 + r * 4 + lr) * W + px0 + cc * 8 + lc) * 3;
-                    p[0] = out_accum ? ar[r][cc] : -expm1f(-ar[r][cc]);
-                    p[1] = out_accum ? ag[r][cc] : -expm1f(-ag[r][cc]);
-                    p[2] = out_accum ? ab[r][cc] : -expm1f(-ab[r][cc]);
+                    put_pixel(p, ar[r][cc], out_accum);
+                    put_pixel(p + 1, ag[r][cc], out_accum);
+                    put_pixel(p + 2, ab[r][cc], out_accum);
                 }
             }
         } else {
@@ -611,7 +617,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                     const int rr = k / rowlen, c3 = k - rr * rowlen;
                     const int col = c3 / 3, ch = c3 - col * 3;
                     const float a = __ldcg(&scr[ch * T * T + rr * T + col]);
-                    ot[(int64_t)rr * W * 3 + c3] = out_accum ? a : -expm1f(-a);
+                    put_pixel(&ot[(int64_t)rr * W * 3 + c3], a, out_accum);
                 }
                 __syncwarp();
                 for (int k = lane; k < 3 * T * T; k += 32) scr[k] = 0.0f;

@@ -242,7 +242,16 @@ static float order_key_inv(unsigned k) {
     return f;
 }
 
+// copy_engine: stage page-locked host inputs with asynchronous copies (the copy engine)
+// instead of reading them in place with the preparation kernel: slower alone, but the
+// copy then overlaps kernels that occupy every SM (the out-of-core render).
+static splotch_status create_scene_impl(const splotch_scene_desc *d, splotch_scene **out, bool copy_engine);
+
 extern "C" splotch_status splotch_create_scene(const splotch_scene_desc *d, splotch_scene **out) {
+    return create_scene_impl(d, out, false);
+}
+
+static splotch_status create_scene_impl(const splotch_scene_desc *d, splotch_scene **out, bool copy_engine) {
     if (!out) return fail(SPLOTCH_ERR_INVALID_ARG, "out is NULL");
     splotch_status s = validate_desc(d);
     if (s != SPLOTCH_OK) return s;
@@ -316,7 +325,7 @@ extern "C" splotch_status splotch_create_scene(const splotch_scene_desc *d, splo
         const float *src[5] = {d->x, d->y, d->z, d->h, d->intensity};
         const float *in[5];
         bool copy_in = !d->on_device;
-        if (copy_in) {
+        if (copy_in && !copy_engine) {
             bool pinned = true;
             for (int k = 0; k < 5 && pinned; ++k) {
                 cudaPointerAttributes pa{};
@@ -488,6 +497,11 @@ static splotch_status compose_camera(const splotch_camera *c, float m[12], float
 extern "C" splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], float p[4]) {
     if (!m || !p) return fail(SPLOTCH_ERR_INVALID_ARG, "output is NULL");
     return compose_camera(cam, m, p);
+}
+
+// Output mode of the splat kernels: 0 final transform, 1 write a, 2 add a.
+static int out_mode(int flags) {
+    return (flags & SPLOTCH_OUT_ADD) ? 2 : ((flags & SPLOTCH_OUT_ACCUM) ? 1 : 0);
 }
 
 static splotch_status check_params(const splotch_render_params *pr) {
@@ -777,7 +791,7 @@ static splotch_status render_frame(splotch_scene *sc, const RenderSetup &rs, flo
             if (e != cudaSuccess) s = fail(SPLOTCH_ERR_CUDA, "debug bins: %s", cudaGetErrorString(e));
             break;
         }
-        s = scatter_and_splat(sc, fh, fixed, var, out, (rs.pr.flags & SPLOTCH_OUT_ACCUM) ? 1 : 0, items, st, ev);
+        s = scatter_and_splat(sc, fh, fixed, var, out, out_mode(rs.pr.flags), items, st, ev);
         if (s != SPLOTCH_OK) break;
         if (sync) {
             int64_t *box = host_box();
@@ -890,7 +904,7 @@ static splotch_status plan_enqueue(splotch_plan *pl, float *out, cudaStream_t st
     CUDA_TRY(launch_scan(fr, target_items(sc->dev, fh.T), kMinItemPairs, st));
     CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, st));
     CUDA_TRY(launch_splat(sc->dev_view, fr, (int *)(pl->fixed + fh.o_queue), out,
-                          (pl->rs.pr.flags & SPLOTCH_OUT_ACCUM) ? 1 : 0, pl->grid, st));
+                          out_mode(pl->rs.pr.flags), pl->grid, st));
     CUDA_TRY(cudaMemcpyAsync(pl->box, pl->fixed + fh.o_sizes, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(pl->box + 8, pl->fixed + fh.o_status, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
     return SPLOTCH_OK;
@@ -1139,7 +1153,7 @@ extern "C" splotch_status splotch_render_noalloc(splotch_scene *sc, const splotc
     CUDA_TRY(launch_scan(fr, target_items(sc->dev, T), kMinItemPairs, st));
     CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, st));
     CUDA_TRY(launch_splat(sc->dev_view, fr, (int *)(base + fh.o_queue), out,
-                          (pr.flags & SPLOTCH_OUT_ACCUM) ? 1 : 0, sm_count(dev) * std::max(1, splat_blocks_per_sm(T)), st));
+                          out_mode(pr.flags), sm_count(dev) * std::max(1, splat_blocks_per_sm(T)), st));
     int64_t sizes[8];
     int stat[4];
     CUDA_TRY(cudaMemcpyAsync(sizes, base + fh.o_sizes, sizeof(sizes), cudaMemcpyDeviceToHost, st));
@@ -1150,5 +1164,141 @@ extern "C" splotch_status splotch_render_noalloc(splotch_scene *sc, const splotc
         return fail(SPLOTCH_ERR_CAPACITY,
                     "frame needs %lld particle-tile pairs and %lld split tiles; the fixed %zu-byte workspace holds %lld and %d",
                     (long long)sizes[kSizePairs], (long long)sizes[kSizeSplits], kStaticBytes, (long long)pairs, splits);
+    return SPLOTCH_OK;
+}
+
+// -----------------------------------------------------------------------------------------
+// Out-of-core render: the particle set stays in host memory and is rendered in chunks.
+// Section 3.2 streams data that does not fit the coprocessor in pieces; here the
+// accumulation is a sum over particles in absorption = emission mode (Section 2.1), so
+// chunks add into one image and the final transform runs once.  While chunk k renders on
+// the caller's stream, chunk k + 1 is prepared on a second stream (read in place from
+// page-locked host memory, or staged), so the host-to-device transfer overlaps the render.
+
+// Exact per-species range of the (logged) intensity over the whole set, chunk by chunk.
+static splotch_status streamed_ranges(const splotch_scene_desc *d, int64_t chunk, cudaStream_t st, Mem &mem,
+                                      std::vector<float> &lo, std::vector<float> &hi) {
+    lo.assign(d->n_types, 0.0f);
+    hi.assign(d->n_types, 0.0f);
+    if (d->i_min) {
+        for (int t = 0; t < d->n_types; ++t) lo[t] = d->i_min[t], hi[t] = d->i_max[t];
+        return SPLOTCH_OK;
+    }
+    const size_t kb = align256(sizeof(unsigned) * 2 * d->n_types);
+    cudaPointerAttributes pa{};
+    bool direct = d->on_device != 0;
+    const float *dev_in = d->intensity;
+    if (!direct && cudaPointerGetAttributes(&pa, d->intensity) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer) {
+        direct = true;
+        dev_in = (const float *)pa.devicePointer;
+    }
+    cudaGetLastError();
+    const size_t stage = direct ? 0 : sizeof(float) * (size_t)std::min<int64_t>(chunk, d->n);
+    char *buf = (char *)mem.alloc(kb + stage, st);
+    if (!buf) return fail(SPLOTCH_ERR_OOM, "range staging");
+    unsigned *keys = (unsigned *)buf;
+    std::vector<unsigned> init(2 * d->n_types);
+    for (int t = 0; t < d->n_types; ++t) init[2 * t] = 0xFFFFFFFFu, init[2 * t + 1] = 0u;
+    cudaError_t e = cudaMemcpyAsync(keys, init.data(), sizeof(unsigned) * init.size(), cudaMemcpyHostToDevice, st);
+    for (int64_t b = 0; b < d->n && e == cudaSuccess; b += chunk) {
+        const int64_t len = std::min(chunk, d->n - b);
+        const float *src = dev_in + b;
+        if (!direct) {
+            e = cudaMemcpyAsync(buf + kb, d->intensity + b, sizeof(float) * len, cudaMemcpyHostToDevice, st);
+            src = (const float *)(buf + kb);
+        }
+        for (int t = 0; t < d->n_types && e == cudaSuccess; ++t) {
+            const int64_t a0 = std::max(b, d->type_begin[t]), a1 = std::min(b + len, d->type_begin[t + 1]);
+            if (a1 > a0) e = launch_minmax(0, src - b, a0, a1, d->i_log[t], keys + 2 * t, st);
+        }
+        if (!direct && e == cudaSuccess) e = cudaStreamSynchronize(st);  // staging reused
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(init.data(), keys, sizeof(unsigned) * init.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    mem.release(buf, st);
+    if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "intensity range: %s", cudaGetErrorString(e));
+    for (int t = 0; t < d->n_types; ++t) {
+        lo[t] = init[2 * t] == 0xFFFFFFFFu ? 0.0f : order_key_inv(init[2 * t]);
+        hi[t] = init[2 * t + 1] == 0u ? 0.0f : order_key_inv(init[2 * t + 1]);
+    }
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, int64_t chunk,
+                                                  const splotch_camera *cam, const splotch_render_params *params,
+                                                  float *out, void *stream) {
+    if (!d || !cam || !out) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    if (chunk < 1) return fail(SPLOTCH_ERR_INVALID_ARG, "chunk < 1");
+    splotch_status s = validate_desc(d);
+    if (s != SPLOTCH_OK) return s;
+    splotch_render_params pr = params ? *params : splotch_default_params();
+    s = check_params(&pr);
+    if (s != SPLOTCH_OK) return s;
+    const bool keep_accum = (pr.flags & SPLOTCH_OUT_ACCUM) != 0;
+    const bool add = (pr.flags & SPLOTCH_OUT_ADD) != 0;
+    pr.flags = (pr.flags & ~(SPLOTCH_SYNC | SPLOTCH_TIMING | SPLOTCH_OUT_ACCUM)) | SPLOTCH_OUT_ADD;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    Mem mem;
+    mem.a = d->allocator;
+    mem.dev = dev;
+    std::vector<float> lo, hi;
+    s = streamed_ranges(d, chunk, st, mem, lo, hi);
+    if (s != SPLOTCH_OK) return s;
+    const size_t img = sizeof(float) * 3 * (size_t)cam->width * (size_t)cam->height;
+    if (!add) CUDA_TRY(cudaMemsetAsync(out, 0, img, st));
+
+    cudaStream_t side = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(side);
+        return fail(SPLOTCH_ERR_CUDA, "event");
+    }
+    // the previous chunk's scene is released only once its render is ordered behind this one
+    splotch_scene *prev = nullptr;
+    auto drop = [&](splotch_scene *sc) {
+        if (!sc) return;
+        sc->mem.release(sc->attr, st);
+        sc->mem.release(sc->meta, st);
+        delete sc;
+    };
+    const float *src[5] = {d->x, d->y, d->z, d->h, d->intensity};
+    for (int64_t b = 0; b < d->n && s == SPLOTCH_OK; b += chunk) {
+        const int64_t len = std::min(chunk, d->n - b);
+        splotch_scene_desc cd = *d;
+        cd.n = len;
+        const float *const *p = src;
+        cd.x = p[0] + b, cd.y = p[1] + b, cd.z = p[2] + b, cd.h = p[3] + b, cd.intensity = p[4] + b;
+        std::vector<int64_t> tb(d->n_types + 1);
+        for (int t = 0; t <= d->n_types; ++t) tb[t] = std::min(std::max(d->type_begin[t] - b, (int64_t)0), len);
+        cd.type_begin = tb.data();
+        cd.i_min = lo.data();
+        cd.i_max = hi.data();
+        cd.stream = side;
+        // prepared on the side stream while the previous chunk's scatter and splat run
+        splotch_scene *sc = nullptr;
+        s = create_scene_impl(&cd, &sc, true);
+        if (s != SPLOTCH_OK) break;
+        if (cudaEventRecord(ready, side) != cudaSuccess || cudaStreamWaitEvent(st, ready, 0) != cudaSuccess) {
+            drop(sc);
+            s = fail(SPLOTCH_ERR_CUDA, "stream order");
+            break;
+        }
+        s = splotch_render(sc, cam, 1, &pr, out, st);
+        drop(prev);
+        prev = sc;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && s == SPLOTCH_OK) s = fail(SPLOTCH_ERR_CUDA, "streamed render");
+    drop(prev);
+    cudaEventDestroy(ready);
+    cudaStreamDestroy(side);
+    if (s != SPLOTCH_OK) return s;
+    if (!keep_accum && !add) {
+        CUDA_TRY(launch_final(out, (int64_t)img / sizeof(float), st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
     return SPLOTCH_OK;
 }

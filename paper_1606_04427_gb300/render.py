@@ -21,13 +21,15 @@ from ._lib import check
 class RenderParams:
     """Tile edge (0 = library default), support factor, sigma / support, minimum
     support in pixels; ``accum`` returns the accumulation a instead of 1 - exp(-a);
-    ``sync`` waits for the frame and reports device-side timeouts."""
+    ``add`` adds the accumulation to what the output holds; ``sync`` waits for the frame
+    and reports device-side timeouts."""
     tile: int = 0
     rfac: float = 0.75
     sigma_over_R: float = 0.5
     r_min_px: float = 0.75
     block_particles: int = 0
     accum: bool = False
+    add: bool = False
     sync: bool = False
     graph: bool = False
     timing: bool = False
@@ -40,7 +42,8 @@ class RenderParams:
         p.r_min_px = float(self.r_min_px)
         p.block_particles = int(self.block_particles)
         p.flags = ((_lib.OUT_ACCUM if self.accum else 0) | (_lib.SYNC if self.sync else 0)
-                   | (_lib.PLAN_GRAPH if self.graph else 0) | (_lib.TIMING if self.timing else 0))
+                   | (_lib.PLAN_GRAPH if self.graph else 0) | (_lib.TIMING if self.timing else 0)
+                   | (_lib.OUT_ADD if self.add else 0))
         return p
 
 
@@ -88,6 +91,70 @@ def last_timing():
             "items": int(cnt[1]), "splits": int(cnt[2])}
 
 
+def _scene_desc(ps, storage: str, stream=None, allocator=None):
+    """splotch_scene_desc of a particle set (host numpy arrays or CUDA tensors) and the
+    objects that must stay alive while the library reads it."""
+    keep = []
+
+    def arr(a, dtype):
+        a = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+        keep.append(a)
+        return a.ctypes.data
+
+    on_dev = isinstance(ps.x, torch.Tensor) and ps.x.is_cuda
+    d = _lib.SceneDesc()
+    n = int(ps.x.shape[0])
+    d.n = n
+    tb = np.asarray(ps.type_begin, np.int64)
+    d.n_types = int(tb.shape[0] - 1)
+    d.type_begin = arr(tb, np.int64)
+    for name in ("x", "y", "z", "h", "intensity"):
+        a = getattr(ps, name)
+        if on_dev:
+            a = a.contiguous().float()
+            keep.append(a)
+            setattr(d, name, a.data_ptr() if n > 0 else None)
+        else:
+            setattr(d, name, arr(a, np.float32) if n > 0 else None)
+    d.on_device = 1 if on_dev else 0
+    d.storage = _lib.STORAGE[storage]
+    cms = [np.ascontiguousarray(c, np.float32) for c in ps.cmaps]
+    keep.extend(cms)
+    ptrs = (C.c_void_p * len(cms))(*[c.ctypes.data for c in cms])
+    keep.append(ptrs)
+    d.cmap_rgb = C.cast(ptrs, C.c_void_p)
+    d.cmap_len = arr([c.shape[0] for c in cms], np.int32)
+    d.brightness = arr(ps.brightness, np.float32)
+    d.i_log = arr(ps.i_log, np.int32)
+    if ps.i_min is not None and ps.i_max is not None:
+        d.i_min = arr(ps.i_min, np.float32)
+        d.i_max = arr(ps.i_max, np.float32)
+    if allocator is not None:
+        d.allocator = allocator.c()
+        keep.append(allocator)
+    d.stream = _stream_handle(stream)
+    return d, keep
+
+
+def render_streamed(ps, cam, chunk: int, params: Optional[RenderParams] = None, out: Optional[torch.Tensor] = None,
+                    storage: str = "f32", stream=None, allocator=None) -> torch.Tensor:
+    """Render a particle set that stays where it is (host arrays or CUDA tensors) in
+    chunks of at most ``chunk`` particles, each chunk's accumulation added into one image
+    (splotch_render_streamed).  Returns H x W x 3 on the device."""
+    lib = _lib.load()
+    d, keep = _scene_desc(ps, storage, stream, allocator)
+    H, W = int(cam.height), int(cam.width)
+    if out is None:
+        out = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == H * W * 3
+    p = (params or RenderParams()).c()
+    c = _lib.camera_c(cam)
+    check(lib.splotch_render_streamed(C.byref(d), int(chunk), C.byref(c), C.byref(p), out.data_ptr(),
+                                      _stream_handle(stream)), "render_streamed")
+    del keep
+    return out
+
+
 class Scene:
     """A particle set resident on the GPU (library-owned storage).
 
@@ -99,45 +166,8 @@ class Scene:
         lib = _lib.load()
         self._lib = lib
         self.storage = storage
-        keep = []
-
-        def arr(a, dtype):
-            a = np.ascontiguousarray(np.asarray(a), dtype=dtype)
-            keep.append(a)
-            return a.ctypes.data
-
-        on_dev = isinstance(ps.x, torch.Tensor) and ps.x.is_cuda
-        d = _lib.SceneDesc()
-        n = int(ps.x.shape[0])
-        d.n = n
-        tb = np.asarray(ps.type_begin, np.int64)
-        d.n_types = int(tb.shape[0] - 1)
-        d.type_begin = arr(tb, np.int64)
-        for name in ("x", "y", "z", "h", "intensity"):
-            a = getattr(ps, name)
-            if on_dev:
-                a = a.contiguous().float()
-                keep.append(a)
-                setattr(d, name, a.data_ptr() if n > 0 else None)
-            else:
-                setattr(d, name, arr(a, np.float32) if n > 0 else None)
-        d.on_device = 1 if on_dev else 0
-        d.storage = _lib.STORAGE[storage]
-        cms = [np.ascontiguousarray(c, np.float32) for c in ps.cmaps]
-        keep.extend(cms)
-        ptrs = (C.c_void_p * len(cms))(*[c.ctypes.data for c in cms])
-        keep.append(ptrs)
-        d.cmap_rgb = C.cast(ptrs, C.c_void_p)
-        d.cmap_len = arr([c.shape[0] for c in cms], np.int32)
-        d.brightness = arr(ps.brightness, np.float32)
-        d.i_log = arr(ps.i_log, np.int32)
-        if ps.i_min is not None and ps.i_max is not None:
-            d.i_min = arr(ps.i_min, np.float32)
-            d.i_max = arr(ps.i_max, np.float32)
-        if allocator is not None:
-            d.allocator = allocator.c()
-            keep.append(allocator)
-        d.stream = _stream_handle(stream)
+        d, keep = _scene_desc(ps, storage, stream, allocator)
+        n = int(d.n)
         h = C.c_void_p()
         check(lib.splotch_create_scene(C.byref(d), C.byref(h)), "create_scene")
         self._h = h

@@ -170,3 +170,51 @@ def test_scene_from_page_locked_host_memory_equals_pageable():
     assert torch.equal(got, pageable) or torch.abs(got - pageable).max().item() <= 1e-6
     ref = oracle.final(oracle.render(ps, cam, oracle.Params(), "f16"))
     assert np.abs(got.numpy() - ref).max() <= 2e-3
+
+
+def _no_ranges(ps):
+    out = ps.with_brightness(ps.brightness)
+    out.i_min = None
+    out.i_max = None
+    return out
+
+
+def test_streamed_render_equals_resident_render():
+    """Out-of-core render in chunks that cut through a species boundary equals the render
+    of the whole resident set (a sum over particles), for given and for computed intensity
+    ranges, from pageable and from page-locked host arrays; and it matches the oracle."""
+    ps = synth.two_species_set(30000, 10000, 11, grid=32).with_brightness([0.05, 0.3])
+    cam = synth.front_camera(200, 150)
+    whole = render.Scene(ps, "f32").render(cam).cpu()
+    for chunk in (7000, 16384, 40000):
+        got = render.render_streamed(ps, cam, chunk).cpu()
+        assert torch.abs(got - whole).max().item() <= 1e-4, chunk
+    free = _no_ranges(ps)
+    whole_free = render.Scene(free, "f32").render(cam).cpu()
+    got = render.render_streamed(free, cam, 9000).cpu()
+    assert torch.abs(got - whole_free).max().item() <= 1e-4
+    pinned = ps.with_brightness(ps.brightness)
+    keep = []
+    for k in ("x", "y", "z", "h", "intensity"):
+        t = torch.from_numpy(np.ascontiguousarray(getattr(ps, k))).pin_memory()
+        keep.append(t)
+        setattr(pinned, k, t.numpy())
+    got16 = render.render_streamed(pinned, cam, 12000, storage="f16").cpu().numpy()
+    ref = oracle.final(oracle.render(ps, cam, oracle.Params(), "f16"))
+    assert np.abs(got16 - ref).max() <= 2e-3
+    acc = render.render_streamed(ps, cam, 8000, render.RenderParams(accum=True)).cpu()
+    whole_acc = render.Scene(ps, "f32").render(cam, render.RenderParams(accum=True)).cpu()
+    assert torch.allclose(acc, whole_acc, rtol=2e-5, atol=1e-7)
+
+
+def test_additive_output_sums_renders():
+    """SPLOTCH_OUT_ADD adds the accumulation to the output: two additive renders of the
+    same frame give twice the accumulation."""
+    ps = synth.clustered_set(30000, 12, grid=32).with_brightness([0.05])
+    cam = synth.front_camera(128, 96)
+    sc = render.Scene(ps, "f32")
+    acc = sc.render(cam, render.RenderParams(accum=True))
+    out = torch.zeros_like(acc)
+    sc.render(cam, render.RenderParams(add=True), out)
+    sc.render(cam, render.RenderParams(add=True), out)
+    assert torch.allclose(out, 2 * acc, rtol=1e-6, atol=1e-7)
