@@ -184,8 +184,8 @@ splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], flo
 splotch_status splotch_render(splotch_scene *scene, const splotch_camera *cams, int32_t n_views,
                               const splotch_render_params *params, float *out, void *stream);
 
-/* Out-of-core render of one view (Section 3.2: data larger than the accelerator's memory is
- * processed in pieces).  The particle set `desc` stays where it is (host or device, as for
+/* Out-of-core render of one view (Section 3.1: data sets larger than the accelerator's memory
+ * go through it in double-buffered pieces, transfers overlapping work).  The particle set `desc` stays where it is (host or device, as for
  * splotch_create_scene) and is rendered in chunks of at most `chunk` particles: each chunk
  * is prepared on the device (page-locked host inputs read in place) on a side stream while
  * the previous chunk renders on `stream`, and its accumulation is added to `out`.  With

@@ -1169,7 +1169,8 @@ extern "C" splotch_status splotch_render_noalloc(splotch_scene *sc, const splotc
 
 // -----------------------------------------------------------------------------------------
 // Out-of-core render: the particle set stays in host memory and is rendered in chunks.
-// Section 3.2 streams data that does not fit the coprocessor in pieces; here the
+// Section 3.1 moves data sets larger than the coprocessor's memory through it in
+// double-buffered pieces, transfers overlapping work; here the
 // accumulation is a sum over particles in absorption = emission mode (Section 2.1), so
 // chunks add into one image and the final transform runs once.  While chunk k renders on
 // the caller's stream, chunk k + 1 is prepared on a second stream (read in place from
