@@ -5,27 +5,33 @@
 // draw adds particle colour x scalar weight to the pixel.  Section 2.1: the weight is
 // a Gaussian of the distance to the particle centre over the radius-dependent area.
 //
-// GB300 layout: one persistent CTA per SM slot pulls work items from a queue.  A work
-// item is a tile, or a K-record slice of a crowded tile (so dense clusters do not
-// serialise on one CTA).  The item's records are staged from HBM into shared memory by
-// bulk copies (cp.async.bulk, double buffered, mbarrier completion with a bounded wait).
-//
-// Pixel ownership goes one level further than the paper's thread-per-tile: the tile is
-// cut into 8 x 4 pixel blocks, block row r belongs to warp r mod 8, and each lane owns
-// one pixel of each of its warp's blocks, accumulating it in registers.  Per stage:
-//   1. decode: one lane per record computes the record's pixel box inside the tile, its
-//      colour (brightness x colormap) and Gaussian scale, and appends the record to the
-//      list of every warp owning a block row the box meets;
-//   2. gather: each warp walks its list; for every block of its own that the box
-//      overlaps, each lane tests its pixel with the FP32 coverage rule and adds e * w
-//      to its registers.  No atomics: a pixel has exactly one owner.
+// GB300 layout: persistent CTAs pull work items from a queue.  A work item is a tile,
+// or a K-record slice of a crowded tile (so dense clusters do not serialise on one
+// worker); slices of a split tile add their partial sums into a scratch tile and the
+// last slice to finish writes the result.  Records are staged from HBM into shared
+// memory by bulk copies (cp.async.bulk, double buffered, mbarrier completion with a
+// bounded wait).  The paper's worker is a thread; here pixels are owned by lanes, each
+// accumulating its pixels in registers (no atomics: a pixel has exactly one owner), in
+// blocks of 8 x 4 pixels, one pixel of each block per lane.  Two kernels:
+//   k_splat_warp  tiles up to 32 px: one warp owns a square of up to 16 x 16 pixels (a
+//                 tile, or a quarter of a larger one) and runs its records grouped by
+//                 the rectangle of blocks they cover (below);
+//   k_splat       tiles above 32 px: the 8 warps of a CTA share a tile by block rows,
+//                 each record queued to the warps whose rows it meets.
 // In clustered data most pixels receive hundreds of contributions per frame, where a
-// shared-memory scatter would serialise on atomic conflicts.  At the end of the item the
-// lanes write 1 - exp(-a) for their pixels; slices of a split tile add their partial
-// sums into a scratch tile and the last slice to finish writes the result.
+// shared-memory scatter would serialise on atomic conflicts.
 #include "splotch_internal.cuh"
 
 namespace spl {
+
+// ---------------------------------------------------------------------------------------
+// CTA-per-item splat for tiles above 32 px.  Per stage of kStage records:
+//   1. decode: one thread per record computes the record's pixel box inside the tile, its
+//      colour (brightness x colormap) and Gaussian scale, and appends the record to the
+//      list of every warp owning a block row the box meets (block row r: warp r mod 8);
+//   2. gather: each warp walks its list; for every block of its own that the box
+//      overlaps, each lane tests its pixel with the FP32 coverage rule and adds e * w
+//      to its registers.
 
 struct __align__(16) Rec {
     int ilo, ihi, jlo, jhi;  // tile-local box

@@ -20,9 +20,9 @@ constexpr int kMaxTiles = 16384;   // tiles per image (per-CTA shared histogram)
 constexpr int kMaxTile = 64;       // tile edge in pixels (shared accumulator)
 constexpr int kMaxTypes = 255;     // species (8-bit type field in the tile records)
 constexpr int kThreads = 1024;     // CTA size of the particle-stream kernels (one per SM: one tile histogram per SM)
-constexpr int kSplatThreads = 256; // CTA size of the splat kernel
+constexpr int kSplatThreads = 256; // CTA size of the splat kernel for tiles above 32 px
 constexpr int kSplatWarps = kSplatThreads / 32;
-constexpr int kStage = 512;        // tile records per bulk-copy stage
+constexpr int kStage = 512;        // tile records per bulk-copy stage (tiles above 32 px)
 constexpr int kMaxGroup = 16;      // views per CTA in the particle-stream kernels
 constexpr uint32_t kCodeMax = 16777215u;   // 24-bit normalised-intensity code
 constexpr float kLog2e = 1.4426950408889634f;
