@@ -236,6 +236,14 @@ splotch_status splotch_plan_create(splotch_scene *scene, const splotch_camera *c
 splotch_status splotch_plan_set_cameras(splotch_plan *plan, const splotch_camera *cams,
                                         int32_t n_views, void *stream);
 
+/* Per-view brightness of a plan (Section 2.1: a scene file varies parameters such as the
+ * brightness over a progression of images that make a movie).  scale: host,
+ * n_views x n_types floats (view-major), each finite and >= 0: the emission of species t
+ * in view v is multiplied by scale[v * n_types + t]; NULL resets every scale to 1.  The
+ * next launch (or graph replay) renders with these scales.  Synchronises `stream`.
+ * Errors: INVALID_ARG (NULL plan, a negative or non-finite scale), CUDA. */
+splotch_status splotch_plan_set_brightness(splotch_plan *plan, const float *scale, void *stream);
+
 /* Enqueue one batch render into out (device, n_views x H x W x 3 FP32). */
 splotch_status splotch_plan_launch(splotch_plan *plan, float *out, void *stream);
 

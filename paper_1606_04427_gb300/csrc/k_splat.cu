@@ -189,9 +189,10 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 q.Y = Y;
                 q.R2 = __fmul_rn(R, R);
                 q.kr = __fdividef(kexp, q.R2);
-                q.er = (1.0f - tau) * c0.x + tau * c1.x;
-                q.eg = (1.0f - tau) * c0.y + tau * c1.y;
-                q.eb = (1.0f - tau) * c0.z + tau * c1.z;
+                const float vs = fr.vscale ? __ldg(&fr.vscale[v * sc.n_types + type]) : 1.0f;
+                q.er = ((1.0f - tau) * c0.x + tau * c1.x) * vs;
+                q.eg = ((1.0f - tau) * c0.y + tau * c1.y) * vs;
+                q.eb = ((1.0f - tau) * c0.z + tau * c1.z) * vs;
                 q.pad = 0.0f;
                 s_rec[idx] = q;
                 const int br0 = q.jlo >> 2, br1 = q.jhi >> 2;
@@ -419,7 +420,9 @@ __device__ __forceinline__ void run_dispatch(int id, const WarpSmem *ws, int j0,
 #undef SPL_RUNS4
 #undef SPL_RUN
 
-template <int NR, int NC>
+// kViewScale: multiply every record's emission by a per-view, per-species scale (plans
+// with a brightness sequence); a separate instance, so plain renders carry no extra code.
+template <int NR, int NC, bool kViewScale>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCtas))
     k_splat_warp(SceneDev sc, FrameDev fr, int *queue, float *out, int out_accum, int split) {
     if (fr.status[kStatOverflow]) return;
@@ -561,10 +564,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 const float4 c0 = __ldg(&sc.lut[lo]);
                 const float4 c1 = __ldg(&sc.lut[lo + 1]);
                 const float R2 = __fmul_rn(R, R);
+                float vs = 1.0f;
+                if constexpr (kViewScale) vs = __ldg(&fr.vscale[v * sc.n_types + type]);
                 float4 *d = reinterpret_cast<float4 *>(&ws->dec[j]);  // in grouped order
                 d[0] = make_float4(rec.x, rec.y, R2, __fdividef(kexp, R2));
-                d[1] = make_float4((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
-                                   (1.0f - tau) * c0.z + tau * c1.z, 0.0f);
+                d[1] = make_float4(((1.0f - tau) * c0.x + tau * c1.x) * vs, ((1.0f - tau) * c0.y + tau * c1.y) * vs,
+                                   ((1.0f - tau) * c0.z + tau * c1.z) * vs, 0.0f);
             }
             __syncwarp();
             // ---- 3. one jump per rectangle present, then its records
@@ -643,7 +648,10 @@ constexpr int kWarpTileMax = 32;
 static bool warp_kernel(int T) { return T <= kWarpTileMax; }
 int splat_split(int T) { return T > 16 && warp_kernel(T) ? 2 : 1; }
 
-static WarpSplatFn warp_fn(int T) { return T <= 8 ? k_splat_warp<2, 1> : k_splat_warp<4, 2>; }
+static WarpSplatFn warp_fn(int T, bool scaled = false) {
+    if (scaled) return T <= 8 ? k_splat_warp<2, 1, true> : k_splat_warp<4, 2, true>;
+    return T <= 8 ? k_splat_warp<2, 1, false> : k_splat_warp<4, 2, false>;
+}
 
 static SplatFn cta_fn(int T) {
     switch (block_cols(T)) {
@@ -673,10 +681,13 @@ int splat_workers_per_sm(int T) { return splat_blocks_per_sm(T) * (warp_kernel(T
 cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, float *out, int out_accum,
                          int grid, cudaStream_t st) {
     const size_t smem = splat_smem(fr.T);
-    cudaError_t err = ensure_smem_limit(splat_kernel(fr.T), smem);
+    const bool scaled = fr.vscale != nullptr;
+    cudaError_t err = ensure_smem_limit(
+        warp_kernel(fr.T) ? (const void *)warp_fn(fr.T, scaled) : splat_kernel(fr.T), smem);
     if (err != cudaSuccess) return err;
     if (warp_kernel(fr.T))
-        warp_fn(fr.T)<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum, splat_split(fr.T));
+        warp_fn(fr.T, scaled)<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum,
+                                                                             splat_split(fr.T));
     else
         cta_fn(fr.T)<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum);
     return cudaGetLastError();

@@ -891,12 +891,14 @@ struct splotch_plan {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     float *exec_out = nullptr;
+    float *vscale = nullptr;  // device [V * n_types] emission scale per view and species
 };
 
 static splotch_status plan_enqueue(splotch_plan *pl, float *out, cudaStream_t st) {
     splotch_scene *sc = pl->sc;
     FrameHost &fh = pl->fh;
     FrameDev fr = frame_dev(fh, pl->fixed, pl->var);
+    fr.vscale = pl->vscale;
     CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_counts, 0, sizeof(int) * (size_t)fh.V * fh.n_tiles, st));
     CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_status, 0, sizeof(int) * 4, st));
     CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_queue, 0, sizeof(int) * 4, st));
@@ -917,6 +919,7 @@ extern "C" splotch_status splotch_plan_destroy(splotch_plan *pl) {
     cudaDeviceSynchronize();
     if (pl->var) pl->sc->mem.release(pl->var, 0);
     if (pl->fixed) pl->sc->mem.release(pl->fixed, 0);
+    if (pl->vscale) pl->sc->mem.release(pl->vscale, 0);
     if (pl->box) cudaFreeHost(pl->box);
     cudaStreamSynchronize(0);
     delete pl;
@@ -970,6 +973,19 @@ extern "C" splotch_status splotch_plan_create(splotch_scene *sc, const splotch_c
         return fail(SPLOTCH_ERR_CUDA, "plan scratch");
     }
     pl->grid = splat_grid(sc->dev, pl->rs.T, INT32_MAX);
+    // emission scale per view and species (1 until splotch_plan_set_brightness): a fixed
+    // device array, so a captured graph reads the current scales at every replay
+    {
+        const size_t nv = (size_t)pl->rs.V * sc->n_types;
+        pl->vscale = (float *)sc->mem.alloc(sizeof(float) * nv, st);
+        std::vector<float> ones(nv, 1.0f);
+        if (!pl->vscale ||
+            cudaMemcpyAsync(pl->vscale, ones.data(), sizeof(float) * nv, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            splotch_plan_destroy(pl);
+            return fail(SPLOTCH_ERR_OOM, "plan view scales");
+        }
+    }
     *out = pl;
     return SPLOTCH_OK;
 }
@@ -988,6 +1004,24 @@ extern "C" splotch_status splotch_plan_set_cameras(splotch_plan *pl, const splot
     CUDA_TRY(cudaMemcpyAsync(pl->fixed + pl->fh.o_views, pl->rs.views.data(), sizeof(ViewParams) * n_views,
                              cudaMemcpyHostToDevice, (cudaStream_t)stream));
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_plan_set_brightness(splotch_plan *pl, const float *scale, void *stream) {
+    if (!pl) return fail(SPLOTCH_ERR_INVALID_ARG, "plan is NULL");
+    const int nt = pl->sc->n_types;
+    const size_t nv = (size_t)pl->rs.V * nt;
+    std::vector<float> v(nv, 1.0f);
+    if (scale)
+        for (size_t k = 0; k < nv; ++k) {
+            if (!(scale[k] >= 0.0f) || !std::isfinite(scale[k]))
+                return fail(SPLOTCH_ERR_INVALID_ARG, "scale[%zu] (view %zu, species %zu) not finite and >= 0", k,
+                            k / nt, k % nt);
+            v[k] = scale[k];
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(pl->vscale, v.data(), sizeof(float) * nv, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
     return SPLOTCH_OK;
 }
 

@@ -77,6 +77,7 @@ struct FrameDev {
     int *tickets;             // [split capacity]
     int64_t pair_cap;
     int item_cap, split_cap;
+    const float *vscale;      // [V * n_types] emission scale per view and species, or null
 };
 
 enum { kSizePairs = 0, kSizeItems = 1, kSizeSplits = 2, kSizeK = 3, kSizeMaxCount = 4 };

@@ -303,6 +303,16 @@ class Plan:
         check(self._lib.splotch_plan_set_cameras(self._h, arr, len(self.cams), _stream_handle(stream)),
               "plan_set_cameras")
 
+    def set_brightness(self, scale=None, stream=None) -> None:
+        """Per-view emission scale per species (n_views x n_types; None resets to 1),
+        applied from the next launch on, graph replays included."""
+        if scale is None:
+            ptr, keep = None, None
+        else:
+            keep = np.ascontiguousarray(np.asarray(scale, np.float32).reshape(len(self.cams), -1))
+            ptr = keep.ctypes.data
+        check(self._lib.splotch_plan_set_brightness(self._h, ptr, _stream_handle(stream)), "plan_set_brightness")
+
     def new_output(self) -> torch.Tensor:
         return torch.empty((self.V, self.H, self.W, 3), dtype=torch.float32, device="cuda")
 

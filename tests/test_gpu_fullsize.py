@@ -70,3 +70,15 @@ def test_batched_64_views_20M_fp16_graph_sampled_views():
         _check(f"batched view {v}", out[v].cpu().numpy(), ps, cams[v], "f16")
     plan.close()
     sc.close()
+
+
+def test_clustered_20M_4096_fp16_quadrant_tiles():
+    """The served stream's largest image: 4096 x 4096 needs 32-px tiles (16384 tiles),
+    which the splat renders as four 16-px squares per tile; a camera at distance 1.1 from
+    the box centre gives large supports and particles past the image edges."""
+    ps = synth.clustered_set(20_000_000, 4).with_brightness([_brightness("served")[4] * 0.3])
+    cam = synth.Camera((0.5, 0.5, 1.6), (0.5, 0.5, 0.5), (0.0, 1.0, 0.0), 45.0, 1e-3, 4096, 4096)
+    sc = render.Scene(ps, "f16")
+    got = sc.render(cam).cpu().numpy()
+    sc.close()
+    _check("clustered 20M 4096^2 FP16 (tile 32, quadrants)", got, ps, cam, "f16")

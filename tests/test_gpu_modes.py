@@ -218,3 +218,29 @@ def test_additive_output_sums_renders():
     sc.render(cam, render.RenderParams(add=True), out)
     sc.render(cam, render.RenderParams(add=True), out)
     assert torch.allclose(out, 2 * acc, rtol=1e-6, atol=1e-7)
+
+
+def test_plan_per_view_brightness_matches_rescaled_scenes():
+    """A brightness sequence over the views of one plan (replayed as a CUDA graph) renders
+    what separate scenes with the scaled brightness render; None restores the scales."""
+    ps = synth.two_species_set(30000, 10000, 13, grid=32).with_brightness([0.05, 0.3])
+    cams = synth.orbit_cameras(3, 128, 96)
+    scale = np.array([[1.0, 1.0], [0.25, 2.0], [0.0, 0.7]], np.float32)
+    sc = render.Scene(ps, "f32")
+    plan = render.Plan(sc, cams, render.RenderParams(), graph=True)
+    out = plan.new_output()
+    plan.launch(out)
+    plain = out.clone()
+    plan.set_brightness(scale)
+    plan.launch(out)
+    plan.check()
+    for v, cam in enumerate(cams):
+        want = render.Scene(ps.with_brightness(ps.brightness * scale[v]), "f32").render(cam)
+        assert torch.abs(out[v] - want).max().item() <= 1e-4, v
+    plan.set_brightness(None)
+    plan.launch(out)
+    plan.check()
+    assert torch.abs(out - plain).max().item() <= 1e-6
+    with pytest.raises(_lib.SplotchError):
+        plan.set_brightness(np.full((3, 2), -1.0, np.float32))
+    plan.close()
