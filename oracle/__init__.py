@@ -68,6 +68,8 @@ def _bind(path: str):
     lib.orc_bin.argtypes = scene + [i32, P, P, P, i64, P]
     lib.orc_covered_pixels.argtypes = scene + [i64, P, i64]
     lib.orc_covered_pixels.restype = i64
+    lib.orc_render_rt_depth.argtypes = scene + [P, P]
+    lib.orc_render_rt_depth.restype = i32
     lib.orc_count_work.argtypes = scene + [i32, P]
     lib.orc_count_work.restype = i32
     lib.orc_final.argtypes = [i64, P, P]
@@ -251,6 +253,17 @@ def render(ps, cam, params: Params = Params(), storage: str = "f32", method: str
         raise ValueError(method)
     assert rc == 0, rc
     return a
+
+
+def render_rt_depth(ps, cam, absorb, params: Params = Params(), storage: str = "f32"):
+    """Image from the radiative-transfer update applied in depth order, farthest first,
+    with absorption = absorb[t] x emission for species t (H x W x 3, FP64)."""
+    s = _Scene(ps, cam, params, storage)
+    ab = np.ascontiguousarray(np.broadcast_to(np.asarray(absorb, np.float64), (s.nt,)))
+    I = np.zeros((s.H, s.W, 3), np.float64)
+    rc = _cur().orc_render_rt_depth(*s.args(), _ptr(ab), _ptr(I))
+    assert rc == 0
+    return I
 
 
 def render_rt_sequential(ps, cam, params: Params = Params(), storage: str = "f32",

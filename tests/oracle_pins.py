@@ -382,6 +382,62 @@ def pin_rt_update_matches_closed_form():
     assert np.abs(I2 - (1.0 - np.exp(-3.0 * a)) / 3.0).max() <= 1e-12
 
 
+def _two_species_cloud(seed, n=2400):
+    """Random cloud split into two species with different colormaps."""
+    rng = np.random.default_rng(seed)
+    cm0 = np.array([[0.2, 0.4, 0.9], [0.9, 0.3, 0.1]], np.float32)
+    cm1 = np.array([[1.0, 0.9, 0.3], [0.1, 0.8, 0.5]], np.float32)
+    ps = make_set(rng.uniform(0, 1, n), rng.uniform(0, 1, n), rng.uniform(0, 1, n),
+                  np.exp(rng.uniform(np.log(0.004), np.log(0.04), n)), rng.uniform(0, 1, n),
+                  type_begin=[0, n // 3, n], cmaps=[cm0, cm1], betas=[0.6, 1.4])
+    return ps, front(80, 60)
+
+
+def pin_rt_depth_closed_forms():
+    """Depth-ordered transfer with one absorption factor s for every species telescopes to
+    (1/s)(1 - exp(-s a)) whatever the order (s = 1: the final transform 1 - exp(-a)), and
+    to the additive sum a when nothing absorbs (s = 0)."""
+    ps, cam = _two_species_cloud(3)
+    a = oracle.render(ps, cam)
+    assert a.max() > 0.5
+    for s in (1.0, 0.4, 2.5):
+        I = oracle.render_rt_depth(ps, cam, [s, s])
+        assert np.abs(I - (1.0 - np.exp(-s * a)) / s).max() <= 1e-12, s
+    assert np.abs(oracle.render_rt_depth(ps, cam, [1.0, 1.0]) - oracle.final(a)).max() <= 1e-12
+    assert np.abs(oracle.render_rt_depth(ps, cam, [0.0, 0.0]) - a).max() <= 1e-12
+
+
+def pin_rt_depth_order_two_particles():
+    """Two overlapping particles of species with different absorption, both centred on one
+    pixel centre (weight 1 there): the far one is applied first from black, the near one
+    on top, I = I1 exp(-A2) + (E2/A2)(1 - exp(-A2)) with I1 = (E1/A1)(1 - exp(-A1)) per
+    channel.  Swapping their depths swaps the roles and changes the pixel."""
+    W = H = 64
+    X, Y = 32.5, 30.5
+    cm = np.array([[0.3, 0.6, 0.9], [0.3, 0.6, 0.9]], np.float32)
+    s_abs = [2.0, 0.25]
+    for far, near, depths in ((0, 1, (3.0, 1.5)), (1, 0, (1.5, 3.0))):
+        pts = [world_for_screen(X, Y, W, H, depth=d) for d in depths]
+        h = [(6.0 / 0.75) * d / focal(H) for d in depths]
+        ps = make_set([p[0] for p in pts], [p[1] for p in pts], [p[2] for p in pts], h, [0.5, 0.5],
+                      type_begin=[0, 1, 2], cmaps=[cm, cm], betas=[0.8, 1.7])
+        r = oracle.raster(ps, front(W, H))
+        assert r["active"].all()
+        assert abs(r["X"][0] - X) < 1e-4 and abs(r["Y"][1] - Y) < 1e-4
+        I = oracle.render_rt_depth(ps, front(W, H), s_abs)
+        e = r["e"]
+        A1, A2 = s_abs[far] * e[far], s_abs[near] * e[near]
+        I1 = (e[far] / A1) * (1.0 - np.exp(-A1))
+        want = I1 * np.exp(-A2) + (e[near] / A2) * (1.0 - np.exp(-A2))
+        got = I[30, 32]
+        assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max(), (far, got, want)
+    # the same two particles with their depths exchanged render a different pixel
+    pair = [make_set([0.5, 0.5], [0.5, 0.5], z, [0.01, 0.01], [0.5, 0.5], type_begin=[0, 1, 2],
+                     cmaps=[cm, cm], betas=[0.8, 1.7]) for z in ([0.5, 0.55], [0.55, 0.5])]
+    I_a, I_b = (oracle.render_rt_depth(p, front(W, H), s_abs) for p in pair)
+    assert np.abs(I_a - I_b).max() > 1e-3
+
+
 # ----------------------------------------------------------------------------------------
 # colour (Section 2.1: scalar through a runtime colormap) and preprocessing
 

@@ -36,6 +36,10 @@ MUTANTS = {
     "tile_half_side": ("float hd = 0.70710677f * (float)T;", "float hd = 0.25f * (float)T;"),
     "tile_corner_not_centre": ("float cx = ((float)tx + 0.5f) * (float)T;", "float cx = (float)tx * (float)T;"),
     "tile_rule_no_support": ("float thr = o->R + hd;", "float thr = hd;"),
+    "rt_depth_front_first": ("if (za != zb) return za > zb ? -1 : 1;", "if (za != zb) return za > zb ? 1 : -1;"),
+    "rt_depth_one_species": ("const double st = absorb[type_of(&s, k)];", "const double st = absorb[0];"),
+    "rt_depth_emission_over_absorption_dropped": ("v[c] = v[c] * t + (E / A) * (1.0 - t);",
+                                                  "v[c] = v[c] * t + (1.0 - t);"),
     "image_transposed": ("double *q = &a[3 * ((size_t)j * W + i)];\n                    for (int c = 0; c < 3; ++c) q[c] += e[k][c] * w;",
                          "double *q = &a[3 * ((size_t)(i % H) * W + (j % W))];\n                    for (int c = 0; c < 3; ++c) q[c] += e[k][c] * w;"),
     "final_wrong": ("O[i] = -expm1(-a[i]);", "O[i] = 1.0 - exp(-2.0 * a[i]);"),
