@@ -294,6 +294,14 @@ splotch_status splotch_last_timing(double ms[4], int64_t counts[3]);
 splotch_status splotch_render_noalloc(splotch_scene *scene, const splotch_camera *cam,
                                       const splotch_render_params *params, float *out, void *stream);
 
+/* Test hook: stable sort of n (key, value) pairs on the device by key bits
+ * [bit_lo, bit_hi) (a multiple of 8 bits), in place: the least-significant-digit radix
+ * sort that puts the tile lists of the depth-ordered render in depth order.  keys and
+ * vals: device, n each; n < 2^32.  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED, OOM,
+ * CUDA. */
+splotch_status splotch_debug_sort(uint64_t *keys, uint32_t *vals, int64_t n, int32_t bit_lo, int32_t bit_hi,
+                                  void *stream);
+
 /* Static strings. */
 const char *splotch_status_string(splotch_status status);
 const char *splotch_last_error(void);

@@ -1337,3 +1337,33 @@ extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, i
     }
     return SPLOTCH_OK;
 }
+
+// -----------------------------------------------------------------------------------------
+// Test hook for the radix sort the depth-ordered render uses.
+extern "C" splotch_status splotch_debug_sort(uint64_t *keys, uint32_t *vals, int64_t n, int32_t bit_lo,
+                                             int32_t bit_hi, void *stream) {
+    if (n < 0 || (n > 0 && (!keys || !vals))) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL buffer or n < 0");
+    if (bit_lo < 0 || bit_hi > 64 || bit_lo > bit_hi || (bit_hi - bit_lo) % 8 != 0)
+        return fail(SPLOTCH_ERR_INVALID_ARG, "key bits [%d, %d) not a whole number of bytes in [0, 64)", bit_lo, bit_hi);
+    if (n > (int64_t)UINT32_MAX) return fail(SPLOTCH_ERR_UNSUPPORTED, "more than 2^32 pairs");
+    if (n <= 1) return SPLOTCH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    Mem mem;
+    mem.dev = dev;
+    const size_t kb = align256(sizeof(uint64_t) * (size_t)n), vb = align256(sizeof(uint32_t) * (size_t)n);
+    char *buf = (char *)mem.alloc(kb + vb + sort_temp_bytes(n), st);
+    if (!buf) return fail(SPLOTCH_ERR_OOM, "sort buffers");
+    bool alt = false;
+    cudaError_t e = radix_sort_pairs(keys, (uint64_t *)buf, vals, (uint32_t *)(buf + kb), n, bit_lo, bit_hi,
+                                     buf + kb + vb, st, &alt);
+    if (e == cudaSuccess && alt) {
+        e = cudaMemcpyAsync(keys, buf, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vals, buf + kb, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    mem.release(buf, st);
+    if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "sort: %s", cudaGetErrorString(e));
+    return SPLOTCH_OK;
+}

@@ -289,6 +289,12 @@ int bin_ctas_per_sm(int storage, size_t smem);
 // `bytes`, once per (kernel, device).  The limit is process-wide state: renders on other
 // host threads launch the same kernels, so it is only ever raised, never set per launch.
 cudaError_t ensure_smem_limit(const void *kernel, size_t bytes);
+
+// Stable LSD radix sort of (64-bit key, 32-bit value) pairs by key bits [bit_lo, bit_hi)
+// (8 bits per pass); the result is in the alternate buffers when *in_alt.
+size_t sort_temp_bytes(int64_t n);
+cudaError_t radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                             int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt);
 size_t splat_smem_bytes(int T);
 cudaError_t launch_selftest_wait(long long limit, int *result, cudaStream_t st);
 cudaError_t launch_final(float *a, int64_t count, cudaStream_t st);
