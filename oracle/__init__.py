@@ -70,6 +70,8 @@ def _bind(path: str):
     lib.orc_covered_pixels.restype = i64
     lib.orc_render_rt_depth.argtypes = scene + [P, P]
     lib.orc_render_rt_depth.restype = i32
+    lib.orc_render_rt_depth_lattice.argtypes = scene + [P, i32, i32, i32, P]
+    lib.orc_render_rt_depth_lattice.restype = i32
     lib.orc_count_work.argtypes = scene + [i32, P]
     lib.orc_count_work.restype = i32
     lib.orc_final.argtypes = [i64, P, P]
@@ -264,6 +266,19 @@ def render_rt_depth(ps, cam, absorb, params: Params = Params(), storage: str = "
     rc = _cur().orc_render_rt_depth(*s.args(), _ptr(ab), _ptr(I))
     assert rc == 0
     return I
+
+
+def render_rt_depth_lattice(ps, cam, absorb, stride: int, ox: int = 0, oy: int = 0, params: Params = Params(),
+                            storage: str = "f32"):
+    """render_rt_depth at the pixels (ox + stride a, oy + stride b) only: equal to
+    render_rt_depth(...)[oy::stride, ox::stride], for images too large to render whole."""
+    s = _Scene(ps, cam, params, storage)
+    ab = np.ascontiguousarray(np.broadcast_to(np.asarray(absorb, np.float64), (s.nt,)))
+    nx, ny = -(-(s.W - ox) // stride), -(-(s.H - oy) // stride)
+    L = np.zeros((ny, nx, 3), np.float64)
+    rc = _cur().orc_render_rt_depth_lattice(*s.args(), _ptr(ab), ox, oy, stride, _ptr(L))
+    assert rc == 0
+    return L
 
 
 def render_rt_sequential(ps, cam, params: Params = Params(), storage: str = "f32",

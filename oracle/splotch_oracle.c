@@ -468,8 +468,16 @@ static int by_depth(const void *pa, const void *pb)
     return a < b ? -1 : (a > b ? 1 : 0);
 }
 
-int orc_render_rt_depth(SCENE_ARGS, const double *absorb, double *I)
+/* The depth-ordered transfer at the pixels of a lattice only: (ox + stride a,
+ * oy + stride b) for a, b >= 0 inside the image, written to L (ny x nx x 3, FP64,
+ * nx = ceil((W - ox) / stride), ny likewise).  A pixel's value depends only on the
+ * particles that cover it, so the particles whose box holds no lattice pixel are left out
+ * before the depth sort; the rest are applied in the same order, so each lattice pixel
+ * equals the full image's pixel exactly.  For checks of images too large to render whole. */
+int orc_render_rt_depth_lattice(SCENE_ARGS, const double *absorb, int ox, int oy, int stride, double *L)
 {
+    if (stride < 1 || ox < 0 || oy < 0 || ox >= W || oy >= H) return 1;
+    const int nx = (W - ox + stride - 1) / stride, ny = (H - oy + stride - 1) / stride;
     orc_scene s;
     fill_scene(&s, SCENE_PASS);
     double (*e)[3] = (double (*)[3])malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -477,20 +485,29 @@ int orc_render_rt_depth(SCENE_ARGS, const double *absorb, double *I)
     int64_t *ord = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     if (!px || !e || !ord) { free(px); free(e); free(ord); return 2; }
     int64_t na = 0;
-    for (int64_t k = 0; k < n; ++k)
-        if (px[k].active) ord[na++] = k;
+    for (int64_t k = 0; k < n; ++k) {
+        const orc_px *o = &px[k];
+        if (!o->active) continue;
+        /* first lattice column / row at or after the box's start */
+        const int ia = o->i0 <= ox ? 0 : (o->i0 - ox + stride - 1) / stride;
+        const int ja = o->j0 <= oy ? 0 : (o->j0 - oy + stride - 1) / stride;
+        if (ox + ia * stride <= o->i1 && oy + ja * stride <= o->j1) ord[na++] = k;
+    }
     g_sort_px = px;
     qsort(ord, (size_t)na, sizeof(int64_t), by_depth);
-    memset(I, 0, sizeof(double) * 3 * (size_t)W * (size_t)H);
+    memset(L, 0, sizeof(double) * 3 * (size_t)nx * (size_t)ny);
     for (int64_t q = 0; q < na; ++q) {
         const int64_t k = ord[q];
         const orc_px *o = &px[k];
         const double st = absorb[type_of(&s, k)];
-        for (int j = o->j0; j <= o->j1; ++j)
-            for (int i = o->i0; i <= o->i1; ++i) {
+        const int ia = o->i0 <= ox ? 0 : (o->i0 - ox + stride - 1) / stride;
+        const int ja = o->j0 <= oy ? 0 : (o->j0 - oy + stride - 1) / stride;
+        for (int b = ja; b < ny && oy + b * stride <= o->j1; ++b)
+            for (int a = ia; a < nx && ox + a * stride <= o->i1; ++a) {
+                const int i = ox + a * stride, j = oy + b * stride;
                 if (!covered(o, i, j)) continue;
                 double w = weight(o, i, j, sor);
-                double *v = &I[3 * ((size_t)j * W + i)];
+                double *v = &L[3 * ((size_t)b * nx + a)];
                 for (int c = 0; c < 3; ++c) {
                     double E = e[k][c], A = st * e[k][c];
                     if (A > 0.0) {
@@ -506,6 +523,13 @@ int orc_render_rt_depth(SCENE_ARGS, const double *absorb, double *I)
     free(px);
     free(e);
     return ORC_OK;
+}
+
+/* The whole image: the lattice of stride 1. */
+int orc_render_rt_depth(SCENE_ARGS, const double *absorb, double *I)
+{
+    if (W <= 0 || H <= 0) return ORC_OK;
+    return orc_render_rt_depth_lattice(SCENE_PASS, absorb, 0, 0, 1, I);
 }
 
 /* Brute force: every pixel against every particle, no box and no tiles; coverage is the

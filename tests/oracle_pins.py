@@ -438,6 +438,50 @@ def pin_rt_depth_order_two_particles():
     assert np.abs(I_a - I_b).max() > 1e-3
 
 
+def pin_rt_depth_equal_depths_in_index_order():
+    """Two particles of different species at exactly the same depth on one pixel centre:
+    the lower index is applied first (the reading taken for equal depths), so the pixel
+    is the two-step closed form with particle 0 underneath; listing the species the other
+    way round puts particle 1's species underneath."""
+    W = H = 64
+    X, Y = 20.5, 40.5
+    cm = np.array([[0.3, 0.6, 0.9], [0.3, 0.6, 0.9]], np.float32)
+    s_abs = [2.0, 0.25]
+    pt = world_for_screen(X, Y, W, H, depth=2.0)
+    h = (5.0 / 0.75) * 2.0 / focal(H)
+    for betas in ((0.8, 1.7), (1.7, 0.8)):
+        ps = make_set([pt[0]] * 2, [pt[1]] * 2, [pt[2]] * 2, [h, h], [0.5, 0.5], type_begin=[0, 1, 2],
+                      cmaps=[cm, cm], betas=list(betas))
+        r = oracle.raster(ps, front(W, H))
+        assert r["active"].all() and r["zc"][0] == r["zc"][1]
+        e = r["e"]
+        A0, A1 = s_abs[0] * e[0], s_abs[1] * e[1]
+        I0 = (e[0] / A0) * (1.0 - np.exp(-A0))
+        want = I0 * np.exp(-A1) + (e[1] / A1) * (1.0 - np.exp(-A1))
+        got = oracle.render_rt_depth(ps, front(W, H), s_abs)[40, 20]
+        assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max(), (betas, got, want)
+
+
+def pin_rt_depth_lattice_is_the_full_image_restricted():
+    """The lattice form leaves out only particles that cover no lattice pixel, so each of
+    its pixels equals the whole image's pixel bit for bit, for several offsets and strides,
+    a lattice one pixel wide, and a lattice with a ragged last row and column."""
+    rng = np.random.default_rng(17)
+    n = 6000
+    cm = np.array([[0.2, 0.5, 0.9], [0.9, 0.4, 0.1]], np.float32)
+    ps = make_set(rng.uniform(0.3, 0.7, n), rng.uniform(0.3, 0.7, n),
+                  rng.choice(np.array([0.4, 0.5, 0.6], np.float32), n),
+                  np.exp(rng.uniform(np.log(0.003), np.log(0.03), n)), rng.uniform(0, 1, n),
+                  type_begin=[0, n // 3, n], cmaps=[cm, cm[::-1].copy()], betas=[0.05, 0.2])
+    cam = front(101, 77)
+    absorb = [1.7, 0.0]
+    full = oracle.render_rt_depth(ps, cam, absorb)
+    assert full.max() > 0.05
+    for stride, ox, oy in ((1, 0, 0), (7, 3, 5), (16, 15, 0), (200, 50, 38), (10, 100, 76)):
+        L = oracle.render_rt_depth_lattice(ps, cam, absorb, stride, ox, oy)
+        assert np.array_equal(L, full[oy::stride, ox::stride]), (stride, ox, oy)
+
+
 # ----------------------------------------------------------------------------------------
 # colour (Section 2.1: scalar through a runtime colormap) and preprocessing
 
