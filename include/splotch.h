@@ -184,6 +184,21 @@ splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], flo
 splotch_status splotch_render(splotch_scene *scene, const splotch_camera *cams, int32_t n_views,
                               const splotch_render_params *params, float *out, void *stream);
 
+/* Depth-ordered render of one view with absorption different from emission (Section 2.1:
+ * the image solves the radiative-transfer equation along each line of sight).  Particles
+ * of species t absorb A = absorb[t] x E (absorb: host, n_types floats, finite, >= 0) and
+ * are applied from the farthest to the nearest (z_c descending) from a black background:
+ * I <- I exp(-A w) + (E / A)(1 - exp(-A w)), or I <- I + E w where A = 0.  out: device,
+ * H x W x 3 FP32, receives I (no final transform: with absorb[t] = 1 for every species I
+ * equals 1 - exp(-a) of splotch_render).  Particles at exactly equal depth are applied in
+ * index order.  Tiles up to 32 px (larger: UNSUPPORTED).  Each tile list is put in order
+ * by stable radix sorts (particle index, then depth, then tile); extra device memory
+ * about 52 bytes per particle-tile pair.  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED, OOM,
+ * CUDA, TIMEOUT. */
+splotch_status splotch_render_ordered(splotch_scene *scene, const splotch_camera *cam,
+                                      const splotch_render_params *params, const float *absorb, float *out,
+                                      void *stream);
+
 /* Out-of-core render of one view (Section 3.1: data sets larger than the accelerator's memory
  * go through it in double-buffered pieces, transfers overlapping work).  The particle set `desc` stays where it is (host or device, as for
  * splotch_create_scene) and is rendered in chunks of at most `chunk` particles: each chunk

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB_NAME = "libsplotch_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
-SOURCES = ["k_bin.cu", "k_splat.cu", "k_sort.cu", "splotch_api.cu"]
+SOURCES = ["k_bin.cu", "k_splat.cu", "k_sort.cu", "k_ordered.cu", "splotch_api.cu"]
 HEADERS = [os.path.join(CSRC, "splotch_internal.cuh"), os.path.join(INCLUDE, "splotch.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -44,6 +44,10 @@ __device__ __forceinline__ unsigned order_key(float f) {
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
+// Sort key of a depth z_c such that ascending keys run from the farthest particle to the
+// nearest: the order-preserving unsigned image of the float, complemented.
+__device__ __forceinline__ uint64_t depth_key(float zc) { return (uint64_t)(~order_key(zc)); }
+
 __global__ void k_minmax(const float *__restrict__ I, int64_t begin, int64_t end, int i_log,
                          unsigned *keys) {
     unsigned lo = 0xFFFFFFFFu, hi = 0u;
@@ -451,6 +455,7 @@ __device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x,
         int *cur = s_cur + g * nt;
         float4 *lists = fr.lists + s_vbase[g];
         int *pids = fr.pids ? fr.pids + s_vbase[g] : nullptr;
+        uint64_t *keys = fr.keys ? fr.keys + s_vbase[g] : nullptr;
         Raster r;
         int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
         if (valid && raster_one(vp, x, y, z, h, r)) {
@@ -481,6 +486,13 @@ __device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x,
                 if (m01) pids[p01] = (int)i;
                 if (m11) pids[p11] = (int)i;
             }
+            if (keys) {
+                const uint64_t dk = depth_key(r.zc);
+                if (m00) keys[p00] = ((uint64_t)t00 << 32) | dk;
+                if (m10) keys[p10] = ((uint64_t)(t00 + 1) << 32) | dk;
+                if (m01) keys[p01] = ((uint64_t)(t00 + vp.ntx) << 32) | dk;
+                if (m11) keys[p11] = ((uint64_t)(t00 + vp.ntx + 1) << 32) | dk;
+            }
         }
         uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
         while (big) {
@@ -490,6 +502,7 @@ __device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x,
             const float bR = __shfl_sync(0xffffffffu, r.R, src);
             const float bcode = __shfl_sync(0xffffffffu, code, src);
             const int bid = __shfl_sync(0xffffffffu, (int)i, src);
+            const float bz = __shfl_sync(0xffffffffu, r.zc, src);
             const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
             const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
             const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
@@ -501,6 +514,7 @@ __device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x,
                     const int pos = atomicAdd(&cur[t], 1);
                     lists[pos] = rec;
                     if (pids) pids[pos] = bid;
+                    if (keys) keys[pos] = ((uint64_t)t << 32) | depth_key(bz);
                 }
             }
         }

@@ -1,0 +1,346 @@
+// Depth-ordered splat: radiative transfer with absorption different from emission.
+//
+// Section 2.1 renders by solving the radiative-transfer equation along each line of
+// sight.  With absorption A equal to emission E every particle's update commutes and the
+// image is 1 - exp(-a) of a plain sum; with A = s_t E for species t (s_t >= 0) it does
+// not, and the particles must be applied in depth order, farthest first, from a black
+// background:
+//     I <- a I + b,   a = exp(-A w),   b = (E / A)(1 - a) = (1 - a) / s_t   (I + E w if s_t = 0)
+// per pixel and channel, w the particle's Gaussian weight there.  The tile lists reach
+// this kernel sorted far to near by stable radix passes: particle index, then the depth
+// key the scatter writes, then the tile, so particles of exactly equal depth keep index
+// order.
+//
+// Layout as the additive warp kernel: one warp owns a square of up to 16 x 16 pixels (a
+// tile, or a quarter of a larger one), blocks of 8 x 4 pixels, one pixel of each block
+// per lane, state in registers.  Records are taken 32 at a time (decoded one per lane)
+// and applied strictly in list order.  Each lane keeps, per pixel and channel, the affine
+// map of the records applied so far, I_out = alpha I_in + beta: a tile that is not split
+// writes beta; the slices of a split tile store their maps, and the last slice to finish
+// composes them far to near.
+#include "splotch_internal.cuh"
+
+namespace spl {
+
+constexpr int kOWarps = 4;     // warps per CTA
+constexpr int kOStage = 128;   // records per bulk copy, per warp
+constexpr int kONR = 4, kONC = 2;  // block rows x block columns of a 16 x 16 square
+constexpr float kOFar = 1e30f;
+
+struct __align__(16) ORec {
+    float X, Y, R2, kr;       // centre, support^2, Gaussian scale (w = 2^(d^2 kr))
+    float kar, kag, kab, inv_s;  // a = 2^(ka w) per channel; 1 / s (0 when s = 0)
+    float e0r, e0g, e0b;      // emission added directly when s = 0 (else 0)
+    uint32_t mask;            // blocks (r * kONC + c) the record's box overlaps
+};
+
+struct __align__(16) OWarpSmem {
+    float4 buf[2][kOStage];
+    ORec dec[32];
+    uint64_t bar[2];
+};
+
+__device__ __forceinline__ int find_tile_o(const int *__restrict__ item_off, int N, int item) {
+    int a = 0, b = N - 1;  // last gt with item_off[gt] <= item
+    while (a < b) {
+        const int m = (a + b + 1) >> 1;
+        if (__ldg(&item_off[m]) <= item) a = m; else b = m - 1;
+    }
+    return a;
+}
+
+__global__ void __launch_bounds__(kOWarps * 32, 4)
+    k_splat_ordered(SceneDev sc, FrameDev fr, int *queue, float *out, int split,
+                    const float *__restrict__ absorb, float *ord_scratch) {
+    if (fr.status[kStatOverflow]) return;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    OWarpSmem *ws = reinterpret_cast<OWarpSmem *>(s_raw) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int nt = fr.n_tiles;
+    const int N = fr.V * nt;
+    const int S2 = split * split;
+    const int total_items = (int)fr.sizes[kSizeItems] * S2;
+    const int64_t K = fr.sizes[kSizeK];
+    const ViewParams g0 = fr.views[0];
+    const int T = g0.T, W = g0.W, H = g0.H, ntx = g0.ntx;
+    const int sub = (T + split - 1) / split;
+    const int lc = lane & 7, lr = lane >> 3;
+
+    if (lane == 0) {
+        mbar_init(&ws->bar[0], 1);
+        mbar_init(&ws->bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    uint32_t phase0 = 0, phase1 = 0;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(queue, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total_items) break;
+
+        const int slice = item / S2, q = item - slice * S2;
+        const int gt = find_tile_o(fr.item_off, N, slice);
+        const int v = gt / nt, t = gt - v * nt;
+        const int chunk = slice - fr.item_off[gt];
+        const int arrivals = (fr.item_off[gt + 1] - fr.item_off[gt]) * S2;
+        const int slot = fr.split_slot[gt];
+        const float kexp = fr.views[v].kexp;
+        const int tx = t % ntx, ty = t / ntx;
+        const int qx = (q % split) * sub, qy = (q / split) * sub;
+        const int px0 = tx * T + qx, py0 = ty * T + qy;
+        const int tw = max(0, min(min(sub, T - qx), W - px0));
+        const int th = max(0, min(min(sub, T - qy), H - py0));
+        const int64_t seg1 = fr.offsets[gt + 1];
+        const int64_t e0 = fr.offsets[gt] + (int64_t)chunk * K;
+        const int nrec = (tw > 0 && th > 0) ? (int)(min(seg1, e0 + K) - e0) : 0;
+        const int nst = (nrec + kOStage - 1) / kOStage;
+
+        float fx[kONC], fy[kONR], al[kONR][kONC][3], be[kONR][kONC][3];
+#pragma unroll
+        for (int c = 0; c < kONC; ++c) fx[c] = c * 8 + lc < tw ? (float)(px0 + c * 8 + lc) + 0.5f : kOFar;
+#pragma unroll
+        for (int r = 0; r < kONR; ++r) {
+            fy[r] = r * 4 + lr < th ? (float)(py0 + r * 4 + lr) + 0.5f : kOFar;
+#pragma unroll
+            for (int c = 0; c < kONC; ++c)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) al[r][c][ch] = 1.0f, be[r][c][ch] = 0.0f;
+        }
+
+        if (lane == 0 && nrec > 0) {
+            const int c0 = min(kOStage, nrec);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&ws->bar[0], (uint32_t)c0 * 16u);
+            bulk_g2s(ws->buf[0], fr.lists + e0, (uint32_t)c0 * 16u, &ws->bar[0]);
+        }
+        for (int si = 0; si < nst; ++si) {
+            const int cb = si & 1;
+            if (lane == 0 && si + 1 < nst) {
+                const int nb = (si + 1) & 1;
+                const int cn = min(kOStage, nrec - (si + 1) * kOStage);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&ws->bar[nb], (uint32_t)cn * 16u);
+                bulk_g2s(ws->buf[nb], fr.lists + e0 + (int64_t)(si + 1) * kOStage, (uint32_t)cn * 16u,
+                         &ws->bar[nb]);
+            }
+            const bool ok = mbar_wait_bounded(&ws->bar[cb], cb ? phase1 : phase0, kWaitCycles);
+            if (cb) phase1 ^= 1u; else phase0 ^= 1u;
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) atomicExch(&fr.status[kStatTimeout], 1);
+                return;
+            }
+            const int cnt = min(kOStage, nrec - si * kOStage);
+            for (int g = 0; g < cnt; g += 32) {
+                // ---- decode: one record per lane
+                uint32_t mask = 0;
+                if (g + lane < cnt) {
+                    const float4 rec = ws->buf[cb][g + lane];
+                    const float X = rec.x, Y = rec.y, R = rec.z;
+                    const uint32_t code = __float_as_uint(rec.w);
+                    const float eps = 1e-3f + 2e-6f * (fabsf(X) + fabsf(Y) + R);
+                    const int ilo = max(0, (int)ceilf(clampf(X - R - 0.5f - eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
+                    const int ihi = min(tw - 1, (int)floorf(clampf(X + R - 0.5f + eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
+                    const int jlo = max(0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))) - py0);
+                    const int jhi = min(th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))) - py0);
+                    if (ilo <= ihi && jlo <= jhi) {
+                        const uint32_t cm = (2u << (ihi >> 3)) - (1u << (ilo >> 3));
+                        for (int r = jlo >> 2; r <= (jhi >> 2); ++r) mask |= cm << (r * kONC);
+                        const int type = (int)(code >> 24);
+                        const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
+                        const int len = __ldg(&sc.lut_len[type]);
+                        const float f = It * (float)(len - 1);
+                        const int kk = min((int)f, len - 2);
+                        const float tau = f - (float)kk;
+                        const int lo = __ldg(&sc.lut_off[type]) + kk;
+                        const float4 c0 = __ldg(&sc.lut[lo]);
+                        const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                        const float er = (1.0f - tau) * c0.x + tau * c1.x, eg = (1.0f - tau) * c0.y + tau * c1.y;
+                        const float eb = (1.0f - tau) * c0.z + tau * c1.z;
+                        const float s = __ldg(&absorb[type]);
+                        const float R2 = __fmul_rn(R, R);
+                        float4 *d = reinterpret_cast<float4 *>(&ws->dec[lane]);
+                        d[0] = make_float4(X, Y, R2, __fdividef(kexp, R2));
+                        d[1] = make_float4(-s * er * kLog2e, -s * eg * kLog2e, -s * eb * kLog2e, s > 0.0f ? 1.0f / s : 0.0f);
+                        d[2] = make_float4(s > 0.0f ? 0.0f : er, s > 0.0f ? 0.0f : eg, s > 0.0f ? 0.0f : eb,
+                                           __uint_as_float(mask));
+                    }
+                }
+                uint32_t live = __ballot_sync(0xffffffffu, mask != 0);
+                __syncwarp();
+                // ---- apply the live records in list order (far to near)
+                while (live) {
+                    const int k = __ffs(live) - 1;
+                    live &= live - 1;
+                    const float4 pa = *reinterpret_cast<const float4 *>(&ws->dec[k].X);
+                    const float4 pk = *reinterpret_cast<const float4 *>(&ws->dec[k].kar);
+                    const float4 pe = *reinterpret_cast<const float4 *>(&ws->dec[k].e0r);
+                    const uint32_t m = __float_as_uint(pe.w);
+#pragma unroll
+                    for (int r = 0; r < kONR; ++r) {
+                        if (!(m & (((1u << kONC) - 1u) << (r * kONC)))) continue;
+                        const float dy = __fsub_rn(fy[r], pa.y);
+                        const float dy2 = __fmul_rn(dy, dy);
+#pragma unroll
+                        for (int c = 0; c < kONC; ++c) {
+                            if (!(m & (1u << (r * kONC + c)))) continue;
+                            const float dx = __fsub_rn(fx[c], pa.x);
+                            const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2);
+                            float w = ex2_fast(d2 * pa.w);
+                            w = d2 < pa.z ? w : 0.0f;  // uncovered: a = 1, b = 0
+                            const float ka[3] = {pk.x, pk.y, pk.z}, e0[3] = {pe.x, pe.y, pe.z};
+#pragma unroll
+                            for (int ch = 0; ch < 3; ++ch) {
+                                // a = exp(-x), x = s E w; 1 - a from its series where x is
+                                // small (1 - a in FP32 would cancel most digits there)
+                                const float t = ka[ch] * w;
+                                const float x = t * -0.69314718f;
+                                const bool small = x < 0.015f;
+                                const float om = small ? x * (1.0f - 0.5f * x * (1.0f - x * (1.0f / 3.0f)))
+                                                       : 1.0f - ex2_fast(t);
+                                const float a = 1.0f - om;
+                                const float b = fmaf(om, pk.w, e0[ch] * w);
+                                al[r][c][ch] *= a;
+                                be[r][c][ch] = fmaf(a, be[r][c][ch], b);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+
+        // epilogue: a whole tile writes I = beta (black background); a slice of a split
+        // tile stores its map, and the last slice composes the tile far to near
+        float *o = out + (int64_t)v * H * W * 3;
+        if (slot < 0) {
+#pragma unroll
+            for (int r = 0; r < kONR; ++r) {
+                if (r * 4 + lr >= th) continue;
+#pragma unroll
+                for (int c = 0; c < kONC; ++c) {
+                    if (c * 8 + lc >= tw) continue;
+                    float *p = o + ((int64_t)(py0 + r * 4 + lr) * W + px0 + c * 8 + lc) * 3;
+                    p[0] = be[r][c][0];
+                    p[1] = be[r][c][1];
+                    p[2] = be[r][c][2];
+                }
+            }
+        } else {
+            float *map = ord_scratch + (int64_t)slice * 6 * T * T;  // [alpha r g b, beta r g b][T][T]
+#pragma unroll
+            for (int r = 0; r < kONR; ++r) {
+                if (r * 4 + lr >= th) continue;
+#pragma unroll
+                for (int c = 0; c < kONC; ++c) {
+                    if (c * 8 + lc >= tw) continue;
+                    const int pix = (qy + r * 4 + lr) * T + qx + c * 8 + lc;
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        map[ch * T * T + pix] = al[r][c][ch];
+                        map[(3 + ch) * T * T + pix] = be[r][c][ch];
+                    }
+                }
+            }
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = (atomicAdd(&fr.tickets[slot], 1) == arrivals - 1);
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                const int TW = min(T, W - tx * T), TH = min(T, H - ty * T);
+                const int s0 = fr.item_off[gt], s1 = fr.item_off[gt + 1];
+                float *ot = o + ((int64_t)ty * T * W + (int64_t)tx * T) * 3;
+                for (int k = lane; k < TH * TW * 3; k += 32) {
+                    const int pix3 = k / 3, ch = k - pix3 * 3;
+                    const int rr = pix3 / TW, col = pix3 - rr * TW;
+                    const int pix = rr * T + col;
+                    float I = 0.0f;
+                    for (int sl = s0; sl < s1; ++sl) {
+                        const float *ms = ord_scratch + (int64_t)sl * 6 * T * T;
+                        I = fmaf(__ldcg(&ms[ch * T * T + pix]), I, __ldcg(&ms[(3 + ch) * T * T + pix]));
+                    }
+                    ot[(int64_t)rr * W * 3 + col * 3 + ch] = I;
+                }
+                if (lane == 0) fr.tickets[slot] = 0;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_iota(uint32_t *v, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (uint32_t)i;
+}
+
+__global__ void k_gather_records(const float4 *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n,
+                                 float4 *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+
+__global__ void k_widen_index(const int *__restrict__ pid, int64_t n, uint64_t *key) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        key[i] = (uint64_t)(uint32_t)pid[i];
+}
+
+__global__ void k_gather_keys(const uint64_t *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n,
+                              uint64_t *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+
+static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)); }
+
+cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_iota<<<grid_for(n), 256, 0, st>>>(v, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_records(const float4 *src, const uint32_t *idx, int64_t n, float4 *dst, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_gather_records<<<grid_for(n), 256, 0, st>>>(src, idx, n, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_widen_index(const int *pid, int64_t n, uint64_t *key, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_widen_index<<<grid_for(n), 256, 0, st>>>(pid, n, key);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_keys(const uint64_t *src, const uint32_t *idx, int64_t n, uint64_t *dst, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_gather_keys<<<grid_for(n), 256, 0, st>>>(src, idx, n, dst);
+    return cudaGetLastError();
+}
+
+int ordered_split(int T) { return T > 16 ? 2 : 1; }
+
+static size_t ordered_smem() { return sizeof(OWarpSmem) * kOWarps; }
+
+int ordered_ctas_per_sm() {
+    if (ensure_smem_limit((const void *)k_splat_ordered, ordered_smem()) != cudaSuccess) return 1;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_splat_ordered, kOWarps * 32, ordered_smem()) !=
+        cudaSuccess)
+        return 1;
+    return std::max(1, nb);
+}
+
+int ordered_workers_per_sm() { return ordered_ctas_per_sm() * kOWarps; }
+
+cudaError_t launch_splat_ordered(const SceneDev &sc, const FrameDev &fr, int *queue, float *out,
+                                 const float *absorb, float *ord_scratch, int grid, cudaStream_t st) {
+    cudaError_t err = ensure_smem_limit((const void *)k_splat_ordered, ordered_smem());
+    if (err != cudaSuccess) return err;
+    k_splat_ordered<<<grid, kOWarps * 32, ordered_smem(), st>>>(sc, fr, queue, out, ordered_split(fr.T), absorb,
+                                                                ord_scratch);
+    return cudaGetLastError();
+}
+
+}  // namespace spl

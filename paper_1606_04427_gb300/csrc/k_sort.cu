@@ -3,7 +3,8 @@
 // The depth-ordered render (Section 2.1: with absorption different from emission the
 // transfer equation must be applied along each line of sight in order) needs every tile
 // list in depth order.  Records carry the key (tile << 32) | depth key; sorting the depth
-// bits and then the tile bits, each pass stable, gives tile-major, far-to-near order.
+// bits and then the tile bits, each pass stable, gives tile-major, far-to-near order (a
+// first sort by particle index makes equal depths keep index order).
 //
 // One pass over 8 key bits:
 //   k_digit_hist   each CTA counts the digits of its 4096 elements (warp-aggregated

@@ -702,7 +702,8 @@ static splotch_status setup_views(const splotch_camera *cams, int n_views, const
 
 // Count + scan for all views and read the sizes back (blocking).
 static splotch_status count_and_size(splotch_scene *sc, const RenderSetup &rs, FrameHost &fh, char *fixed,
-                                     cudaStream_t st, int64_t sizes[8], cudaEvent_t *ev = nullptr) {
+                                     cudaStream_t st, int64_t sizes[8], cudaEvent_t *ev = nullptr,
+                                     int scan_target = 0) {
     FrameDev fr = frame_dev(fh, fixed, nullptr);
     CUDA_TRY(cudaMemcpyAsync(fixed + fh.o_views, rs.views.data(), sizeof(ViewParams) * rs.V,
                              cudaMemcpyHostToDevice, st));
@@ -711,7 +712,7 @@ static splotch_status count_and_size(splotch_scene *sc, const RenderSetup &rs, F
     if (ev) CUDA_TRY(cudaEventRecord(ev[0], st));
     CUDA_TRY(launch_count(sc->storage, sc->dev_view, fr, st));
     if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
-    CUDA_TRY(launch_scan(fr, target_items(sc->dev, fh.T), kMinItemPairs, st));
+    CUDA_TRY(launch_scan(fr, scan_target > 0 ? scan_target : target_items(sc->dev, fh.T), kMinItemPairs, st));
     if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
     int64_t *box = host_box();
     if (!box) return fail(SPLOTCH_ERR_OOM, "pinned host buffer");
@@ -1365,5 +1366,105 @@ extern "C" splotch_status splotch_debug_sort(uint64_t *keys, uint32_t *vals, int
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     mem.release(buf, st);
     if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "sort: %s", cudaGetErrorString(e));
+    return SPLOTCH_OK;
+}
+
+// -----------------------------------------------------------------------------------------
+// Depth-ordered render (absorption != emission).  Section 2.1 solves the radiative-transfer
+// equation along each line of sight; with absorption A = s_t x emission per species the
+// particles' updates do not commute, so every tile list is put in depth order (farthest
+// first) before the splat: the scatter writes a (tile, depth) key per record, a stable
+// radix sort orders the keys, and the records are gathered in that order.
+extern "C" splotch_status splotch_render_ordered(splotch_scene *sc, const splotch_camera *cam,
+                                                 const splotch_render_params *params, const float *absorb,
+                                                 float *out, void *stream) {
+    if (!sc || !cam || !absorb || !out) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    for (int t = 0; t < sc->n_types; ++t)
+        if (!(absorb[t] >= 0.0f) || !std::isfinite(absorb[t]))
+            return fail(SPLOTCH_ERR_INVALID_ARG, "absorb[%d] not finite and >= 0", t);
+    RenderSetup rs;
+    splotch_status s = setup_views(cam, 1, params, rs);
+    if (s != SPLOTCH_OK) return s;
+    if (rs.T > 32) return fail(SPLOTCH_ERR_UNSUPPORTED, "depth-ordered render: tile %d above 32 px", rs.T);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int split = ordered_split(rs.T);
+    const int target = std::max(1, sm_count(sc->dev) * ordered_workers_per_sm() * 4 / (split * split));
+    FrameHost fh;
+    layout_fixed(fh, sc, 1, rs.views[0].n_tiles, rs.T, rs.pr.block_particles);
+    char *fixed = (char *)sc->mem.alloc(fh.fixed_bytes, st);
+    if (!fixed) return fail(SPLOTCH_ERR_OOM, "frame workspace (%zu bytes)", fh.fixed_bytes);
+    int64_t sizes[8];
+    s = count_and_size(sc, rs, fh, fixed, st, sizes, nullptr, target);
+    if (s != SPLOTCH_OK) {
+        sc->mem.release(fixed, st);
+        return s;
+    }
+    const int64_t P = sizes[kSizePairs];
+    const int items = (int)sizes[kSizeItems], splits = (int)sizes[kSizeSplits];
+    if (P > (int64_t)UINT32_MAX) {
+        sc->mem.release(fixed, st);
+        return fail(SPLOTCH_ERR_UNSUPPORTED, "depth-ordered render: more than 2^32 particle-tile pairs");
+    }
+    layout_var(fh, P, items, splits, true);
+    Carve cv;
+    const size_t o_kd = cv.take(sizeof(uint64_t) * (size_t)std::max<int64_t>(1, P));
+    const size_t o_k0 = cv.take(sizeof(uint64_t) * (size_t)std::max<int64_t>(1, P));
+    const size_t o_k1 = cv.take(sizeof(uint64_t) * (size_t)std::max<int64_t>(1, P));
+    const size_t o_v0 = cv.take(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, P));
+    const size_t o_v1 = cv.take(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, P));
+    const size_t o_rec = cv.take(sizeof(float4) * (size_t)std::max<int64_t>(1, P));
+    const size_t o_map = cv.take(sizeof(float) * 6 * (size_t)rs.T * rs.T * (size_t)std::max(1, items));
+    const size_t o_abs = cv.take(sizeof(float) * (size_t)sc->n_types);
+    const size_t o_tmp = cv.take(sort_temp_bytes(std::max<int64_t>(2, P)));
+    char *var = (char *)sc->mem.alloc(fh.var_bytes, st);
+    char *ex = var ? (char *)sc->mem.alloc(cv.off, st) : nullptr;
+    if (!var || !ex) {
+        if (var) sc->mem.release(var, st);
+        sc->mem.release(fixed, st);
+        return fail(SPLOTCH_ERR_OOM, "ordered render workspace (%zu + %zu bytes)", fh.var_bytes, cv.off);
+    }
+    cudaError_t e = cudaMemsetAsync(var + fh.o_scratch, 0, fh.var_bytes - fh.o_scratch, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fixed + fh.o_queue, 0, sizeof(int) * 4, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ex + o_abs, absorb, sizeof(float) * sc->n_types, cudaMemcpyHostToDevice, st);
+    FrameDev fr = frame_dev(fh, fixed, var);
+    fr.keys = (uint64_t *)(ex + o_kd);
+    if (e == cudaSuccess) e = launch_scatter(sc->storage, sc->dev_view, fr, st);
+    if (e == cudaSuccess) e = launch_iota((uint32_t *)(ex + o_v0), P, st);
+    uint64_t *ka = (uint64_t *)(ex + o_k0), *kb = (uint64_t *)(ex + o_k1);
+    uint32_t *va = (uint32_t *)(ex + o_v0), *vb = (uint32_t *)(ex + o_v1);
+    bool alt = false;
+    // particle index first (records of equal depth then stay in index order, as the
+    // definition applies them), then the depth bits, then the tile bits; every pass is
+    // stable, and each sorts only as many 8-bit digits as its largest value needs
+    int ibits = 8, tbits = 8;
+    while (ibits < 32 && (sc->n >> ibits) > 0) ibits += 8;
+    while (tbits < 32 && ((int64_t)(rs.views[0].n_tiles - 1) >> tbits) > 0) tbits += 8;
+    if (e == cudaSuccess) e = launch_widen_index(fr.pids, P, ka, st);
+    if (e == cudaSuccess) e = radix_sort_pairs(ka, kb, va, vb, P, 0, ibits, ex + o_tmp, st, &alt);
+    if (alt) std::swap(ka, kb), std::swap(va, vb);
+    if (e == cudaSuccess) e = launch_gather_keys((const uint64_t *)(ex + o_kd), va, P, ka, st);
+    if (e == cudaSuccess) e = radix_sort_pairs(ka, kb, va, vb, P, 0, 32, ex + o_tmp, st, &alt);
+    if (alt) std::swap(ka, kb), std::swap(va, vb);
+    if (e == cudaSuccess) e = radix_sort_pairs(ka, kb, va, vb, P, 32, 32 + tbits, ex + o_tmp, st, &alt);
+    if (alt) std::swap(ka, kb), std::swap(va, vb);
+    float4 *sorted = (float4 *)(ex + o_rec);
+    if (e == cudaSuccess) e = launch_gather_records(fr.lists, va, P, sorted, st);
+    fr.lists = sorted;
+    fr.keys = nullptr;
+    const int64_t squares = (int64_t)std::max(1, items) * split * split;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count(sc->dev) * ordered_ctas_per_sm(),
+                                                                (squares + 3) / 4));
+    if (e == cudaSuccess)
+        e = launch_splat_ordered(sc->dev_view, fr, (int *)(fixed + fh.o_queue), out, (const float *)(ex + o_abs),
+                                 (float *)(ex + o_map), grid, st);
+    int stat[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stat, fixed + fh.o_status, sizeof(stat), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    sc->mem.release(ex, st);
+    sc->mem.release(var, st);
+    sc->mem.release(fixed, st);
+    if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "ordered render: %s", cudaGetErrorString(e));
+    if (stat[kStatTimeout]) return fail(SPLOTCH_ERR_TIMEOUT, "splat stage wait timed out");
     return SPLOTCH_OK;
 }

@@ -217,6 +217,21 @@ class Scene:
                                                _stream_handle(stream)), "render_noalloc")
         return out
 
+    def render_ordered(self, cam, absorb, params: Optional[RenderParams] = None, out: Optional[torch.Tensor] = None,
+                       stream=None) -> torch.Tensor:
+        """Depth-ordered radiative transfer with absorption = absorb[t] x emission for
+        species t, farthest particle first (splotch_render_ordered).  Returns H x W x 3."""
+        H, W = int(cam.height), int(cam.width)
+        if out is None:
+            out = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == H * W * 3
+        ab = np.ascontiguousarray(np.broadcast_to(np.asarray(absorb, np.float32), (self.n_types,)))
+        p = (params or RenderParams()).c()
+        c = _lib.camera_c(cam)
+        check(self._lib.splotch_render_ordered(self.handle, C.byref(c), C.byref(p), ab.ctypes.data, out.data_ptr(),
+                                               _stream_handle(stream)), "render_ordered")
+        return out
+
     def debug_raster(self, cam, params: Optional[RenderParams] = None, stream=None):
         out = torch.empty((8, max(1, self.n)), dtype=torch.float32, device="cuda")
         p = (params or RenderParams()).c()

@@ -82,3 +82,22 @@ def test_clustered_20M_4096_fp16_quadrant_tiles():
     got = sc.render(cam).cpu().numpy()
     sc.close()
     _check("clustered 20M 4096^2 FP16 (tile 32, quadrants)", got, ps, cam, "f16")
+
+
+def test_two_species_100M_2048_fp16_depth_ordered_lattice():
+    """The depth-ordered render (absorption 1.5 and 0.3 times the emission) of the
+    benchmark frame, against the oracle's ordered transfer on a lattice of 128 x 128
+    pixels (every 16th pixel from (5, 9)); the oracle applies the particles covering those
+    pixels far to near, in FP64."""
+    ps = synth.two_species_set(70_000_000, 30_000_000, 2).with_brightness(_brightness("two_species"))
+    cam = synth.front_camera(2048, 2048)
+    absorb = [1.5, 0.3]
+    sc = render.Scene(ps, "f16")
+    got = sc.render_ordered(cam, absorb).cpu().numpy()[9::16, 5::16]
+    sc.close()
+    ref = oracle.render_rt_depth_lattice(ps, cam, absorb, 16, 5, 9, storage="f16")
+    err = float(np.abs(got - ref).max())
+    print(f"\nordered 100M 2048^2 FP16 lattice: max |I - I_oracle| = {err:.3e} (bar 2e-03), "
+          f"mean I {float(ref.mean()):.4f}")
+    assert ref.mean() > 1e-2
+    assert err <= TOL_O["f16"], err

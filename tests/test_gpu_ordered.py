@@ -46,3 +46,99 @@ def test_radix_sort_is_a_stable_sort_by_the_chosen_bits(n):
     k2, v2 = _sorted_on_gpu(k1, v1, 32, 48)
     order = np.lexsort((vals, depth, tile))
     assert np.array_equal(v2, vals[order])
+
+
+import oracle  # noqa: E402
+from paper_1606_04427_gb300 import render, synth  # noqa: E402
+
+TOL_O = {"f32": 1e-4, "f16": 2e-3}
+
+
+def _species_set(seed, n_gas=40000, n_star=15000):
+    return synth.two_species_set(n_gas, n_star, seed, grid=64).with_brightness([0.05, 0.3])
+
+
+def test_ordered_with_unit_absorption_is_the_standard_image():
+    """Absorption = emission for every species: the ordered transfer telescopes to
+    1 - exp(-a), the image of the additive path."""
+    ps = _species_set(21)
+    cam = synth.front_camera(192, 160)
+    sc = render.Scene(ps, "f32")
+    std = sc.render(cam).cpu().numpy()
+    got = sc.render_ordered(cam, [1.0, 1.0]).cpu().numpy()
+    assert np.abs(got - std).max() <= 1e-4
+    # a common factor s: (1 - exp(-s a)) / s
+    a = sc.render(cam, render.RenderParams(accum=True)).cpu().numpy().astype(np.float64)
+    got = sc.render_ordered(cam, [2.5, 2.5]).cpu().numpy()
+    assert np.abs(got - (1.0 - np.exp(-2.5 * a)) / 2.5).max() <= 1e-4
+
+
+@pytest.mark.parametrize("tile", [8, 16, 24, 32])
+def test_ordered_matches_the_depth_ordered_oracle(tile):
+    """Species with different absorption (order matters): against the oracle's transfer
+    applied farthest first, for tiles rendered whole and as four squares."""
+    ps = _species_set(22 + tile)
+    cam = synth.front_camera(200, 150)
+    absorb = [2.0, 0.3]
+    ref = oracle.render_rt_depth(ps, cam, absorb)
+    got = render.Scene(ps, "f32").render_ordered(cam, absorb, render.RenderParams(tile=tile)).cpu().numpy()
+    err = float(np.abs(got - ref).max())
+    assert err <= TOL_O["f32"], (tile, err)
+    # the order matters for this scene: the additive closed form is far off
+    assert np.abs(ref - oracle.final(oracle.render(ps, cam))).max() > 1e-2
+
+
+def test_ordered_split_tiles_compose_their_slices():
+    """A crowded tile is cut into slices of the depth-sorted list; the slices' affine maps
+    compose far to near.  Also zero absorption (additive species) and FP16 storage."""
+    rng = np.random.default_rng(5)
+    n = 60000
+    x = 0.5 + 0.01 * rng.standard_normal(n)
+    y = 0.5 + 0.01 * rng.standard_normal(n)
+    z = rng.uniform(0.2, 0.8, n)
+    h = np.exp(rng.uniform(np.log(0.002), np.log(0.02), n))
+    import oracle_pins as P
+    cm = np.array([[0.2, 0.5, 0.9], [0.9, 0.4, 0.1]], np.float32)
+    ps = P.make_set(x, y, z, h, rng.uniform(0, 1, n), type_begin=[0, n // 2, n], cmaps=[cm, cm[::-1].copy()],
+                    betas=[0.02, 0.05])
+    cam = synth.front_camera(96, 96)
+    for absorb, storage in (([1.5, 0.0], "f32"), ([0.7, 3.0], "f16")):
+        sc = render.Scene(ps, storage)
+        assert sc.debug_bins(cam, render.RenderParams(tile=16))[0].max() > 4096  # split tiles
+        ref = oracle.render_rt_depth(ps, cam, absorb, storage=storage)
+        got = sc.render_ordered(cam, absorb, render.RenderParams(tile=16)).cpu().numpy()
+        assert np.abs(got - ref).max() <= TOL_O[storage], (absorb, storage)
+
+
+@pytest.mark.parametrize("tile", [16, 32])
+def test_ordered_equal_depths_apply_in_index_order(tile):
+    """Particles on three planes of equal depth, the species mixed on each plane: equal
+    depths must be applied in particle-index order, as the oracle does, not in the order
+    the binning's atomics happen to store them."""
+    import oracle_pins as P
+    rng = np.random.default_rng(40 + tile)
+    n = 30000
+    z = rng.choice(np.array([0.35, 0.5, 0.65], np.float32), n)
+    cm = np.array([[0.2, 0.5, 0.9], [0.9, 0.4, 0.1]], np.float32)
+    ps = P.make_set(rng.uniform(0.25, 0.75, n), rng.uniform(0.25, 0.75, n), z,
+                    np.exp(rng.uniform(np.log(0.004), np.log(0.03), n)), rng.uniform(0, 1, n),
+                    type_begin=[0, n // 2, n], cmaps=[cm, cm[::-1].copy()], betas=[0.05, 0.1])
+    cam = synth.front_camera(160, 128)
+    r = oracle.raster(ps, cam)
+    zc = r["zc"][r["active"]]
+    assert np.unique(zc).shape[0] < zc.shape[0] // 100  # nearly every depth is shared
+    absorb = [2.5, 0.2]
+    ref = oracle.render_rt_depth(ps, cam, absorb)
+    got = render.Scene(ps, "f32").render_ordered(cam, absorb, render.RenderParams(tile=tile)).cpu().numpy()
+    assert np.abs(got - ref).max() <= TOL_O["f32"]
+
+
+def test_ordered_rejects_large_tiles_and_bad_absorption():
+    sc = render.Scene(_species_set(30, 2000, 500), "f32")
+    cam = synth.front_camera(128, 128)
+    with pytest.raises(_lib.SplotchError) as e:
+        sc.render_ordered(cam, [1.0, 1.0], render.RenderParams(tile=40))
+    assert e.value.status == _lib.UNSUPPORTED
+    with pytest.raises(_lib.SplotchError) as e:
+        sc.render_ordered(cam, [1.0, -1.0])
+    assert e.value.status == _lib.INVALID_ARG
