@@ -191,10 +191,11 @@ splotch_status splotch_render(splotch_scene *scene, const splotch_camera *cams, 
  * I <- I exp(-A w) + (E / A)(1 - exp(-A w)), or I <- I + E w where A = 0.  out: device,
  * H x W x 3 FP32, receives I (no final transform: with absorb[t] = 1 for every species I
  * equals 1 - exp(-a) of splotch_render).  Particles at exactly equal depth are applied in
- * index order.  Tiles up to 32 px (larger: UNSUPPORTED).  Each tile list is put in order
- * by stable radix sorts (particle index, then depth, then tile); extra device memory
- * about 52 bytes per particle-tile pair.  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED, OOM,
- * CUDA, TIMEOUT. */
+ * index order.  Tiles up to 32 px (larger: UNSUPPORTED).  The particles are sorted by
+ * depth (stable radix sort from index order), their records written out in that order and
+ * grouped by a stable sort on tile id; device memory besides the tile lists: about 52
+ * bytes per particle and 32 per particle-tile pair.  Synchronous.  Errors: INVALID_ARG,
+ * UNSUPPORTED, OOM, CUDA, TIMEOUT. */
 splotch_status splotch_render_ordered(splotch_scene *scene, const splotch_camera *cam,
                                       const splotch_render_params *params, const float *absorb, float *out,
                                       void *stream);
@@ -311,11 +312,11 @@ splotch_status splotch_render_noalloc(splotch_scene *scene, const splotch_camera
 
 /* Test hook: stable sort of n (key, value) pairs on the device by key bits
  * [bit_lo, bit_hi) (a multiple of 8 bits), in place: the least-significant-digit radix
- * sort that puts the tile lists of the depth-ordered render in depth order.  keys and
- * vals: device, n each; n < 2^32.  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED, OOM,
- * CUDA. */
-splotch_status splotch_debug_sort(uint64_t *keys, uint32_t *vals, int64_t n, int32_t bit_lo, int32_t bit_hi,
-                                  void *stream);
+ * sort of the depth-ordered render (particles by depth, then records by tile).  keys:
+ * device, n unsigned integers of key_bytes (4 or 8) bytes each; vals: device, n uint32;
+ * n < 2^32.  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+splotch_status splotch_debug_sort(void *keys, int32_t key_bytes, uint32_t *vals, int64_t n, int32_t bit_lo,
+                                  int32_t bit_hi, void *stream);
 
 /* Static strings. */
 const char *splotch_status_string(splotch_status status);

@@ -46,7 +46,8 @@ __device__ __forceinline__ unsigned order_key(float f) {
 
 // Sort key of a depth z_c such that ascending keys run from the farthest particle to the
 // nearest: the order-preserving unsigned image of the float, complemented.
-__device__ __forceinline__ uint64_t depth_key(float zc) { return (uint64_t)(~order_key(zc)); }
+__device__ __forceinline__ uint32_t depth_key(float zc) { return ~order_key(zc); }
+constexpr uint32_t kInactiveKey = 0xFFFFFFFFu;  // no finite depth in front of the near plane maps here
 
 __global__ void k_minmax(const float *__restrict__ I, int64_t begin, int64_t end, int i_log,
                          unsigned *keys) {
@@ -455,7 +456,6 @@ __device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x,
         int *cur = s_cur + g * nt;
         float4 *lists = fr.lists + s_vbase[g];
         int *pids = fr.pids ? fr.pids + s_vbase[g] : nullptr;
-        uint64_t *keys = fr.keys ? fr.keys + s_vbase[g] : nullptr;
         Raster r;
         int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
         if (valid && raster_one(vp, x, y, z, h, r)) {
@@ -486,13 +486,6 @@ __device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x,
                 if (m01) pids[p01] = (int)i;
                 if (m11) pids[p11] = (int)i;
             }
-            if (keys) {
-                const uint64_t dk = depth_key(r.zc);
-                if (m00) keys[p00] = ((uint64_t)t00 << 32) | dk;
-                if (m10) keys[p10] = ((uint64_t)(t00 + 1) << 32) | dk;
-                if (m01) keys[p01] = ((uint64_t)(t00 + vp.ntx) << 32) | dk;
-                if (m11) keys[p11] = ((uint64_t)(t00 + vp.ntx + 1) << 32) | dk;
-            }
         }
         uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
         while (big) {
@@ -502,7 +495,6 @@ __device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x,
             const float bR = __shfl_sync(0xffffffffu, r.R, src);
             const float bcode = __shfl_sync(0xffffffffu, code, src);
             const int bid = __shfl_sync(0xffffffffu, (int)i, src);
-            const float bz = __shfl_sync(0xffffffffu, r.zc, src);
             const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
             const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
             const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
@@ -514,7 +506,6 @@ __device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x,
                     const int pos = atomicAdd(&cur[t], 1);
                     lists[pos] = rec;
                     if (pids) pids[pos] = bid;
-                    if (keys) keys[pos] = ((uint64_t)t << 32) | depth_key(bz);
                 }
             }
         }
@@ -676,6 +667,198 @@ cudaError_t launch_debug_raster(int storage, const SceneDev &sc, const ViewParam
     if (storage == 0) k_debug_raster<0><<<(int)blocks, 256, 0, st>>>(sc, view, out8);
     else if (storage == 1) k_debug_raster<1><<<(int)blocks, 256, 0, st>>>(sc, view, out8);
     else k_debug_raster<2><<<(int)blocks, 256, 0, st>>>(sc, view, out8);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Depth-ordered binning (one view), for the transfer with absorption different from
+// emission, where every tile list must run from the farthest particle to the nearest.
+//   k_depth_records  per particle: record {X, Y, R, code}, depth key (all ones when the
+//                    particle is not active) and its index;
+//   (stable radix sort of the depth keys with the indices: equal depths keep index order)
+//   k_sorted_counts  in that order: the gathered record and the number of tiles it belongs
+//                    to (plus a zero past the end, so the exclusive scan ends with the total);
+//   (exclusive scan of the counts: each particle's first output slot)
+//   k_expand         each particle's records at its slots, keyed by tile id;
+//   (stable radix sort by tile id: each tile's records stay in depth order)
+
+template <int S>
+__global__ void __launch_bounds__(256) k_depth_records(SceneDev sc, const ViewParams *__restrict__ views,
+                                                       float4 *prec, uint32_t *dkey, uint32_t *pid) {
+    __shared__ ViewParams s_v;
+    __shared__ int64_t s_tb[kMaxTypes + 1];
+    if (threadIdx.x == 0) s_v = views[0];
+    for (int k = threadIdx.x; k <= sc.n_types; k += blockDim.x) s_tb[k] = sc.type_begin[k];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int type = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sc.n; i += stride) {
+        while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
+        Raster r;
+        const bool act = raster_one(s_v, load1<S>(sc.x, i), load1<S>(sc.y, i), load1<S>(sc.z, i),
+                                    load1<S>(sc.h, i), r);
+        prec[i] = make_float4(r.X, r.Y, r.R, record_code(type, load1<S>(sc.it, i)));
+        dkey[i] = act ? (uint32_t)depth_key(r.zc) : kInactiveKey;
+        pid[i] = (uint32_t)i;
+    }
+}
+
+// Tiles of a rasterised particle, in row-major order over its tile box: the first
+// `small` boxes (up to 2 x 2) by one lane, larger ones by the whole warp.
+__device__ __forceinline__ void tile_box(const ViewParams &v, float X, float Y, float R, int &tx0, int &tx1,
+                                         int &ty0, int &ty1) {
+    int i0, i1, j0, j1;
+    pixel_box(v, X, Y, R, i0, i1, j0, j1);
+    tx0 = tile_of(v, i0), tx1 = tile_of(v, i1), ty0 = tile_of(v, j0), ty1 = tile_of(v, j1);
+}
+
+__global__ void __launch_bounds__(256) k_sorted_counts(const ViewParams *__restrict__ views,
+                                                       const float4 *__restrict__ prec,
+                                                       const uint32_t *__restrict__ skey,
+                                                       const uint32_t *__restrict__ spid, int64_t n, float4 *srec,
+                                                       uint32_t *cnt) {
+    __shared__ ViewParams s_v;
+    if (threadIdx.x == 0) s_v = views[0];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[n] = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += wstride) {
+        const int64_t q = base + lane;
+        float4 rec = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+        if (q < n && skey[q] != kInactiveKey) {
+            rec = prec[spid[q]];
+            tile_box(s_v, rec.x, rec.y, rec.z, tx0, tx1, ty0, ty1);
+        }
+        const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
+        uint32_t c = 0;
+        if (small)
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) c += tile_member(s_v, rec.x, rec.y, rec.z, tx, ty) ? 1u : 0u;
+        uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const float bX = __shfl_sync(0xffffffffu, rec.x, src), bY = __shfl_sync(0xffffffffu, rec.y, src);
+            const float bR = __shfl_sync(0xffffffffu, rec.z, src);
+            const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
+            const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
+            const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
+            uint32_t mine = 0;
+            for (int k = lane; k < ncand; k += 32)
+                mine += tile_member(s_v, bX, bY, bR, bx0 + k % bw, by0 + k / bw) ? 1u : 0u;
+            const uint32_t tot = __reduce_add_sync(0xffffffffu, mine);
+            if (lane == src) c = tot;
+        }
+        if (q < n) {
+            srec[q] = rec;
+            cnt[q] = c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_expand(const ViewParams *__restrict__ views,
+                                                const float4 *__restrict__ srec, const uint32_t *__restrict__ poff,
+                                                int64_t n, int64_t P, float4 *recs, uint32_t *tkey, uint32_t *tval,
+                                                int *status) {
+    __shared__ ViewParams s_v;
+    if (threadIdx.x == 0) s_v = views[0];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += wstride) {
+        const int64_t q = base + lane;
+        float4 rec = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        uint32_t o0 = 0, c = 0;
+        int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+        if (q < n) {
+            o0 = poff[q];
+            c = poff[q + 1] - o0;
+            if (c) {
+                rec = srec[q];
+                tile_box(s_v, rec.x, rec.y, rec.z, tx0, tx1, ty0, ty1);
+            }
+        }
+        const bool small = c && tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
+        if (small) {
+            uint32_t k = 0;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    if (!tile_member(s_v, rec.x, rec.y, rec.z, tx, ty)) continue;
+                    const uint32_t pos = o0 + k++;
+                    if (k > c || (int64_t)pos >= P) {
+                        atomicExch(&status[kStatOverflow], 1);
+                        continue;
+                    }
+                    recs[pos] = rec;
+                    tkey[pos] = (uint32_t)(ty * s_v.ntx + tx);
+                    tval[pos] = pos;
+                }
+        }
+        uint32_t big = __ballot_sync(0xffffffffu, c && tx1 >= tx0 && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const float4 b = make_float4(__shfl_sync(0xffffffffu, rec.x, src), __shfl_sync(0xffffffffu, rec.y, src),
+                                         __shfl_sync(0xffffffffu, rec.z, src), __shfl_sync(0xffffffffu, rec.w, src));
+            const uint32_t bo = __shfl_sync(0xffffffffu, o0, src), bc = __shfl_sync(0xffffffffu, c, src);
+            const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
+            const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
+            const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
+            uint32_t k = 0;
+            for (int kb = 0; kb < ncand; kb += 32) {
+                const int kc = kb + lane;
+                const int tx = bx0 + kc % bw, ty = by0 + kc / bw;
+                const bool m = kc < ncand && tile_member(s_v, b.x, b.y, b.z, tx, ty);
+                const uint32_t bal = __ballot_sync(0xffffffffu, m);
+                if (m) {
+                    const uint32_t kk = k + (uint32_t)__popc(bal & lt);
+                    const uint32_t pos = bo + kk;
+                    if (kk >= bc || (int64_t)pos >= P) {
+                        atomicExch(&status[kStatOverflow], 1);
+                    } else {
+                        recs[pos] = b;
+                        tkey[pos] = (uint32_t)(ty * s_v.ntx + tx);
+                        tval[pos] = pos;
+                    }
+                }
+                k += (uint32_t)__popc(bal);
+            }
+        }
+    }
+}
+
+static int stream_grid(int64_t n, int threads) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * (2048 / threads)));
+}
+
+cudaError_t launch_depth_records(int storage, const SceneDev &sc, const ViewParams *views, float4 *prec,
+                                 uint32_t *dkey, uint32_t *pid, cudaStream_t st) {
+    if (sc.n <= 0) return cudaSuccess;
+    const int g = stream_grid(sc.n, 256);
+    if (storage == 0) k_depth_records<0><<<g, 256, 0, st>>>(sc, views, prec, dkey, pid);
+    else if (storage == 1) k_depth_records<1><<<g, 256, 0, st>>>(sc, views, prec, dkey, pid);
+    else k_depth_records<2><<<g, 256, 0, st>>>(sc, views, prec, dkey, pid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sorted_counts(const ViewParams *views, const float4 *prec, const uint32_t *skey,
+                                 const uint32_t *spid, int64_t n, float4 *srec, uint32_t *cnt, cudaStream_t st) {
+    k_sorted_counts<<<stream_grid(std::max<int64_t>(1, n), 256), 256, 0, st>>>(views, prec, skey, spid, n, srec,
+                                                                               cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const ViewParams *views, const float4 *srec, const uint32_t *poff, int64_t n, int64_t P,
+                          float4 *recs, uint32_t *tkey, uint32_t *tval, int *status, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_expand<<<stream_grid(n, 256), 256, 0, st>>>(views, srec, poff, n, P, recs, tkey, tval, status);
     return cudaGetLastError();
 }
 

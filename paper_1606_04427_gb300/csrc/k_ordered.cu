@@ -7,9 +7,9 @@
 // background:
 //     I <- a I + b,   a = exp(-A w),   b = (E / A)(1 - a) = (1 - a) / s_t   (I + E w if s_t = 0)
 // per pixel and channel, w the particle's Gaussian weight there.  The tile lists reach
-// this kernel sorted far to near by stable radix passes: particle index, then the depth
-// key the scatter writes, then the tile, so particles of exactly equal depth keep index
-// order.
+// this kernel far to near, particles of exactly equal depth in index order: the particles
+// are sorted by depth (stably, from index order), their records are written out in that
+// order, and a stable sort by tile id groups them (depth-ordered binning).
 //
 // Layout as the additive warp kernel: one warp owns a square of up to 16 x 16 pixels (a
 // tile, or a quarter of a larger one), blocks of 8 x 4 pixels, one pixel of each block
@@ -271,51 +271,17 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
     }
 }
 
-__global__ void k_iota(uint32_t *v, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v[i] = (uint32_t)i;
-}
-
 __global__ void k_gather_records(const float4 *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n,
                                  float4 *dst) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = src[idx[i]];
 }
 
-__global__ void k_widen_index(const int *__restrict__ pid, int64_t n, uint64_t *key) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        key[i] = (uint64_t)(uint32_t)pid[i];
-}
-
-__global__ void k_gather_keys(const uint64_t *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n,
-                              uint64_t *dst) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[idx[i]];
-}
-
 static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)); }
-
-cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_iota<<<grid_for(n), 256, 0, st>>>(v, n);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_gather_records(const float4 *src, const uint32_t *idx, int64_t n, float4 *dst, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_gather_records<<<grid_for(n), 256, 0, st>>>(src, idx, n, dst);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_widen_index(const int *pid, int64_t n, uint64_t *key, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_widen_index<<<grid_for(n), 256, 0, st>>>(pid, n, key);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gather_keys(const uint64_t *src, const uint32_t *idx, int64_t n, uint64_t *dst, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_gather_keys<<<grid_for(n), 256, 0, st>>>(src, idx, n, dst);
     return cudaGetLastError();
 }
 

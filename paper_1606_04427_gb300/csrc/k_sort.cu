@@ -25,10 +25,13 @@ constexpr int kSortTile = kSortWarps * kSortPerWarp;    // elements per CTA
 constexpr int kSortRounds = kSortPerWarp / 32;
 constexpr int kScanChunk = 4096;                        // entries per CTA in the scan
 
-__device__ __forceinline__ uint32_t digit_of(uint64_t k, int shift) { return (uint32_t)(k >> shift) & 255u; }
+template <typename K> __device__ __forceinline__ uint32_t digit_of(K k, int shift) {
+    return (uint32_t)(k >> shift) & 255u;
+}
 
-__global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t *__restrict__ keys, int64_t n,
-                                                            int shift, int n_blocks, uint32_t *hist) {
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_digit_hist(const K *__restrict__ keys, int64_t n, int shift,
+                                                            int n_blocks, uint32_t *hist) {
     __shared__ uint32_t s_cnt[256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < 256; d += kSortThreads) s_cnt[d] = 0;
@@ -117,11 +120,12 @@ __global__ void k_scan_add(uint32_t *a, int64_t n, const uint32_t *__restrict__ 
     for (int64_t k = i; k < min(n, (int64_t)(blockIdx.x + 1) * kScanChunk); k += blockDim.x) a[k] += s;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const uint64_t *__restrict__ keys,
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const K *__restrict__ keys,
                                                                const uint32_t *__restrict__ vals, int64_t n,
                                                                int shift, int n_blocks,
                                                                const uint32_t *__restrict__ offs,
-                                                               uint64_t *keys_out, uint32_t *vals_out) {
+                                                               K *keys_out, uint32_t *vals_out) {
     __shared__ uint32_t s_wc[kSortWarps][256];  // per warp: running count, then warp base
     __shared__ uint32_t s_off[256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const uint64_t *
     for (int d = threadIdx.x; d < 256; d += kSortThreads) s_off[d] = offs[(int64_t)d * n_blocks + blockIdx.x];
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kSortPerWarp;
-    uint64_t k_r[kSortRounds];
+    K k_r[kSortRounds];
     uint32_t v_r[kSortRounds], rank[kSortRounds];
     const uint32_t lt = (1u << lane) - 1u;
     // rank of each element among the equal digits of its warp's range, in input order
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const uint64_t *
     for (int r = 0; r < kSortRounds; ++r) {
         const int64_t i = base + r * 32 + lane;
         const bool ok = i < n;
-        k_r[r] = ok ? keys[i] : 0ull;
+        k_r[r] = ok ? keys[i] : (K)0;
         v_r[r] = ok ? vals[i] : 0u;
         const uint32_t d = ok ? digit_of(k_r[r], shift) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -183,8 +187,9 @@ size_t sort_temp_bytes(int64_t n) {
 
 // Sorts keys[0, n) with their values by key bits [bit_lo, bit_hi), stably, ping-ponging
 // with the alternate buffers; *in_alt tells which pair of buffers holds the result.
-cudaError_t radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
-                             int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt) {
+template <typename K>
+static cudaError_t sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int bit_lo,
+                             int bit_hi, void *temp, cudaStream_t st, bool *in_alt) {
     *in_alt = false;
     if (n <= 1) return cudaSuccess;
     const int nb = sort_blocks(n);
@@ -192,14 +197,14 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
     const int chunks = (int)((h + kScanChunk - 1) / kScanChunk);
     uint32_t *hist = (uint32_t *)temp;
     uint32_t *sums = hist + h;
-    uint64_t *ka = keys, *kb = keys_alt;
+    K *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
     for (int shift = bit_lo; shift < bit_hi; shift += 8) {
-        k_digit_hist<<<nb, kSortThreads, 0, st>>>(ka, n, shift, nb, hist);
+        k_digit_hist<K><<<nb, kSortThreads, 0, st>>>(ka, n, shift, nb, hist);
         k_scan_chunks<<<chunks, 1024, 0, st>>>(hist, h, sums);
         k_scan_sums<<<1, 1024, 0, st>>>(sums, chunks);
         k_scan_add<<<chunks, 1024, 0, st>>>(hist, h, sums);
-        k_digit_scatter<<<nb, kSortThreads, 0, st>>>(ka, va, n, shift, nb, hist, kb, vb);
+        k_digit_scatter<K><<<nb, kSortThreads, 0, st>>>(ka, va, n, shift, nb, hist, kb, vb);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         std::swap(ka, kb);
@@ -207,6 +212,31 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
         *in_alt = !*in_alt;
     }
     return cudaSuccess;
+}
+
+cudaError_t radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                             int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt) {
+    return sort_impl<uint64_t>(keys, keys_alt, vals, vals_alt, n, bit_lo, bit_hi, temp, st, in_alt);
+}
+
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                             int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt) {
+    return sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, bit_lo, bit_hi, temp, st, in_alt);
+}
+
+size_t scan_temp_bytes(int64_t n) {
+    return sizeof(uint32_t) * (size_t)((std::max<int64_t>(1, n) + kScanChunk - 1) / kScanChunk) + 256;
+}
+
+// In-place exclusive scan of a[0, n) (the total must stay below 2^32).
+cudaError_t exclusive_scan_u32(uint32_t *a, int64_t n, void *temp, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int chunks = (int)((n + kScanChunk - 1) / kScanChunk);
+    uint32_t *sums = (uint32_t *)temp;
+    k_scan_chunks<<<chunks, 1024, 0, st>>>(a, n, sums);
+    k_scan_sums<<<1, 1024, 0, st>>>(sums, chunks);
+    k_scan_add<<<chunks, 1024, 0, st>>>(a, n, sums);
+    return cudaGetLastError();
 }
 
 }  // namespace spl

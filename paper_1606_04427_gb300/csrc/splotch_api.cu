@@ -1341,11 +1341,13 @@ extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, i
 
 // -----------------------------------------------------------------------------------------
 // Test hook for the radix sort the depth-ordered render uses.
-extern "C" splotch_status splotch_debug_sort(uint64_t *keys, uint32_t *vals, int64_t n, int32_t bit_lo,
-                                             int32_t bit_hi, void *stream) {
+extern "C" splotch_status splotch_debug_sort(void *keys, int32_t key_bytes, uint32_t *vals, int64_t n,
+                                             int32_t bit_lo, int32_t bit_hi, void *stream) {
     if (n < 0 || (n > 0 && (!keys || !vals))) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL buffer or n < 0");
-    if (bit_lo < 0 || bit_hi > 64 || bit_lo > bit_hi || (bit_hi - bit_lo) % 8 != 0)
-        return fail(SPLOTCH_ERR_INVALID_ARG, "key bits [%d, %d) not a whole number of bytes in [0, 64)", bit_lo, bit_hi);
+    if (key_bytes != 4 && key_bytes != 8) return fail(SPLOTCH_ERR_INVALID_ARG, "key_bytes %d not 4 or 8", key_bytes);
+    if (bit_lo < 0 || bit_hi > 8 * key_bytes || bit_lo > bit_hi || (bit_hi - bit_lo) % 8 != 0)
+        return fail(SPLOTCH_ERR_INVALID_ARG, "key bits [%d, %d) not a whole number of bytes in [0, %d)", bit_lo,
+                    bit_hi, 8 * key_bytes);
     if (n > (int64_t)UINT32_MAX) return fail(SPLOTCH_ERR_UNSUPPORTED, "more than 2^32 pairs");
     if (n <= 1) return SPLOTCH_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1353,14 +1355,18 @@ extern "C" splotch_status splotch_debug_sort(uint64_t *keys, uint32_t *vals, int
     CUDA_TRY(cudaGetDevice(&dev));
     Mem mem;
     mem.dev = dev;
-    const size_t kb = align256(sizeof(uint64_t) * (size_t)n), vb = align256(sizeof(uint32_t) * (size_t)n);
+    const size_t kb = align256((size_t)key_bytes * (size_t)n), vb = align256(sizeof(uint32_t) * (size_t)n);
     char *buf = (char *)mem.alloc(kb + vb + sort_temp_bytes(n), st);
     if (!buf) return fail(SPLOTCH_ERR_OOM, "sort buffers");
     bool alt = false;
-    cudaError_t e = radix_sort_pairs(keys, (uint64_t *)buf, vals, (uint32_t *)(buf + kb), n, bit_lo, bit_hi,
-                                     buf + kb + vb, st, &alt);
+    cudaError_t e =
+        key_bytes == 8
+            ? radix_sort_pairs((uint64_t *)keys, (uint64_t *)buf, vals, (uint32_t *)(buf + kb), n, bit_lo, bit_hi,
+                               buf + kb + vb, st, &alt)
+            : radix_sort_pairs((uint32_t *)keys, (uint32_t *)buf, vals, (uint32_t *)(buf + kb), n, bit_lo, bit_hi,
+                               buf + kb + vb, st, &alt);
     if (e == cudaSuccess && alt) {
-        e = cudaMemcpyAsync(keys, buf, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+        e = cudaMemcpyAsync(keys, buf, (size_t)key_bytes * (size_t)n, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(vals, buf + kb, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1405,17 +1411,25 @@ extern "C" splotch_status splotch_render_ordered(splotch_scene *sc, const splotc
         sc->mem.release(fixed, st);
         return fail(SPLOTCH_ERR_UNSUPPORTED, "depth-ordered render: more than 2^32 particle-tile pairs");
     }
-    layout_var(fh, P, items, splits, true);
+    layout_var(fh, P, items, splits, false);
+    // depth-ordered binning buffers: per particle (n) and per pair (P)
+    const int64_t n = std::max<int64_t>(1, sc->n), Pm = std::max<int64_t>(1, P);
     Carve cv;
-    const size_t o_kd = cv.take(sizeof(uint64_t) * (size_t)std::max<int64_t>(1, P));
-    const size_t o_k0 = cv.take(sizeof(uint64_t) * (size_t)std::max<int64_t>(1, P));
-    const size_t o_k1 = cv.take(sizeof(uint64_t) * (size_t)std::max<int64_t>(1, P));
-    const size_t o_v0 = cv.take(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, P));
-    const size_t o_v1 = cv.take(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, P));
-    const size_t o_rec = cv.take(sizeof(float4) * (size_t)std::max<int64_t>(1, P));
+    const size_t o_prec = cv.take(sizeof(float4) * (size_t)n);
+    const size_t o_srec = cv.take(sizeof(float4) * (size_t)n);
+    const size_t o_dk0 = cv.take(sizeof(uint32_t) * (size_t)n);
+    const size_t o_dk1 = cv.take(sizeof(uint32_t) * (size_t)n);
+    const size_t o_id0 = cv.take(sizeof(uint32_t) * (size_t)n);
+    const size_t o_id1 = cv.take(sizeof(uint32_t) * (size_t)n);
+    const size_t o_cnt = cv.take(sizeof(uint32_t) * (size_t)(n + 1));
+    const size_t o_rec = cv.take(sizeof(float4) * (size_t)Pm);
+    const size_t o_tk0 = cv.take(sizeof(uint32_t) * (size_t)Pm);
+    const size_t o_tk1 = cv.take(sizeof(uint32_t) * (size_t)Pm);
+    const size_t o_tv0 = cv.take(sizeof(uint32_t) * (size_t)Pm);
+    const size_t o_tv1 = cv.take(sizeof(uint32_t) * (size_t)Pm);
     const size_t o_map = cv.take(sizeof(float) * 6 * (size_t)rs.T * rs.T * (size_t)std::max(1, items));
     const size_t o_abs = cv.take(sizeof(float) * (size_t)sc->n_types);
-    const size_t o_tmp = cv.take(sort_temp_bytes(std::max<int64_t>(2, P)));
+    const size_t o_tmp = cv.take(std::max(sort_temp_bytes(std::max(n, Pm) + 1), scan_temp_bytes(n + 1)));
     char *var = (char *)sc->mem.alloc(fh.var_bytes, st);
     char *ex = var ? (char *)sc->mem.alloc(cv.off, st) : nullptr;
     if (!var || !ex) {
@@ -1428,30 +1442,31 @@ extern "C" splotch_status splotch_render_ordered(splotch_scene *sc, const splotc
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ex + o_abs, absorb, sizeof(float) * sc->n_types, cudaMemcpyHostToDevice, st);
     FrameDev fr = frame_dev(fh, fixed, var);
-    fr.keys = (uint64_t *)(ex + o_kd);
-    if (e == cudaSuccess) e = launch_scatter(sc->storage, sc->dev_view, fr, st);
-    if (e == cudaSuccess) e = launch_iota((uint32_t *)(ex + o_v0), P, st);
-    uint64_t *ka = (uint64_t *)(ex + o_k0), *kb = (uint64_t *)(ex + o_k1);
-    uint32_t *va = (uint32_t *)(ex + o_v0), *vb = (uint32_t *)(ex + o_v1);
+    // particles in depth order (stable from index order: equal depths keep index order)
+    uint32_t *dka = (uint32_t *)(ex + o_dk0), *dkb = (uint32_t *)(ex + o_dk1);
+    uint32_t *ida = (uint32_t *)(ex + o_id0), *idb = (uint32_t *)(ex + o_id1);
     bool alt = false;
-    // particle index first (records of equal depth then stay in index order, as the
-    // definition applies them), then the depth bits, then the tile bits; every pass is
-    // stable, and each sorts only as many 8-bit digits as its largest value needs
-    int ibits = 8, tbits = 8;
-    while (ibits < 32 && (sc->n >> ibits) > 0) ibits += 8;
+    if (e == cudaSuccess)
+        e = launch_depth_records(sc->storage, sc->dev_view, fr.views, (float4 *)(ex + o_prec), dka, ida, st);
+    if (e == cudaSuccess) e = radix_sort_pairs(dka, dkb, ida, idb, sc->n, 0, 32, ex + o_tmp, st, &alt);
+    if (alt) std::swap(dka, dkb), std::swap(ida, idb);
+    // each particle's records at the scanned offsets of its tile counts, keyed by tile
+    uint32_t *cnt = (uint32_t *)(ex + o_cnt);
+    if (e == cudaSuccess)
+        e = launch_sorted_counts(fr.views, (const float4 *)(ex + o_prec), dka, ida, sc->n, (float4 *)(ex + o_srec),
+                                 cnt, st);
+    if (e == cudaSuccess) e = exclusive_scan_u32(cnt, sc->n + 1, ex + o_tmp, st);
+    uint32_t *tka = (uint32_t *)(ex + o_tk0), *tkb = (uint32_t *)(ex + o_tk1);
+    uint32_t *tva = (uint32_t *)(ex + o_tv0), *tvb = (uint32_t *)(ex + o_tv1);
+    if (e == cudaSuccess)
+        e = launch_expand(fr.views, (const float4 *)(ex + o_srec), cnt, sc->n, P, (float4 *)(ex + o_rec), tka, tva,
+                          fr.status, st);
+    // stable by tile id: every tile list keeps depth order
+    int tbits = 8;
     while (tbits < 32 && ((int64_t)(rs.views[0].n_tiles - 1) >> tbits) > 0) tbits += 8;
-    if (e == cudaSuccess) e = launch_widen_index(fr.pids, P, ka, st);
-    if (e == cudaSuccess) e = radix_sort_pairs(ka, kb, va, vb, P, 0, ibits, ex + o_tmp, st, &alt);
-    if (alt) std::swap(ka, kb), std::swap(va, vb);
-    if (e == cudaSuccess) e = launch_gather_keys((const uint64_t *)(ex + o_kd), va, P, ka, st);
-    if (e == cudaSuccess) e = radix_sort_pairs(ka, kb, va, vb, P, 0, 32, ex + o_tmp, st, &alt);
-    if (alt) std::swap(ka, kb), std::swap(va, vb);
-    if (e == cudaSuccess) e = radix_sort_pairs(ka, kb, va, vb, P, 32, 32 + tbits, ex + o_tmp, st, &alt);
-    if (alt) std::swap(ka, kb), std::swap(va, vb);
-    float4 *sorted = (float4 *)(ex + o_rec);
-    if (e == cudaSuccess) e = launch_gather_records(fr.lists, va, P, sorted, st);
-    fr.lists = sorted;
-    fr.keys = nullptr;
+    if (e == cudaSuccess) e = radix_sort_pairs(tka, tkb, tva, tvb, P, 0, tbits, ex + o_tmp, st, &alt);
+    if (alt) std::swap(tka, tkb), std::swap(tva, tvb);
+    if (e == cudaSuccess) e = launch_gather_records((const float4 *)(ex + o_rec), tva, P, fr.lists, st);
     const int64_t squares = (int64_t)std::max(1, items) * split * split;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count(sc->dev) * ordered_ctas_per_sm(),
                                                                 (squares + 3) / 4));
@@ -1465,6 +1480,7 @@ extern "C" splotch_status splotch_render_ordered(splotch_scene *sc, const splotc
     sc->mem.release(var, st);
     sc->mem.release(fixed, st);
     if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "ordered render: %s", cudaGetErrorString(e));
+    if (stat[kStatOverflow]) return fail(SPLOTCH_ERR_CUDA, "depth-ordered binning: tile counts disagree");
     if (stat[kStatTimeout]) return fail(SPLOTCH_ERR_TIMEOUT, "splat stage wait timed out");
     return SPLOTCH_OK;
 }

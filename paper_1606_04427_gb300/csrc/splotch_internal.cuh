@@ -78,7 +78,6 @@ struct FrameDev {
     int64_t pair_cap;
     int item_cap, split_cap;
     const float *vscale;      // [V * n_types] emission scale per view and species, or null
-    uint64_t *keys;           // [pair capacity] (tile << 32) | far-to-near depth key, or null
 };
 
 enum { kSizePairs = 0, kSizeItems = 1, kSizeSplits = 2, kSizeK = 3, kSizeMaxCount = 4 };
@@ -291,23 +290,36 @@ int bin_ctas_per_sm(int storage, size_t smem);
 // host threads launch the same kernels, so it is only ever raised, never set per launch.
 cudaError_t ensure_smem_limit(const void *kernel, size_t bytes);
 
-// Stable LSD radix sort of (64-bit key, 32-bit value) pairs by key bits [bit_lo, bit_hi)
-// (8 bits per pass); the result is in the alternate buffers when *in_alt.
+// Stable LSD radix sort of (64- or 32-bit key, 32-bit value) pairs by key bits
+// [bit_lo, bit_hi) (8 bits per pass); the result is in the alternate buffers when *in_alt.
 size_t sort_temp_bytes(int64_t n);
+cudaError_t radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                             int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt);
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                             int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt);
+// In-place exclusive scan of 32-bit counts whose total stays below 2^32.
+size_t scan_temp_bytes(int64_t n);
+cudaError_t exclusive_scan_u32(uint32_t *a, int64_t n, void *temp, cudaStream_t st);
 
-// Depth-ordered render: record index fill, record gather by sorted index, and the
-// ordered splat (tiles up to 32 px; squares of up to 16 px, split when T > 16).
-cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t st);
+// Depth-ordered binning of one view (views[0]): per-particle records and depth keys, the
+// counts in sorted order (cnt has n + 1 entries, the last set to 0), and the expansion
+// into (tile id, slot) pairs at the scanned offsets; k_expand flags kStatOverflow in
+// `status` if a particle's tiles disagree with its count.
+cudaError_t launch_depth_records(int storage, const SceneDev &sc, const ViewParams *views, float4 *prec,
+                                 uint32_t *dkey, uint32_t *pid, cudaStream_t st);
+cudaError_t launch_sorted_counts(const ViewParams *views, const float4 *prec, const uint32_t *skey,
+                                 const uint32_t *spid, int64_t n, float4 *srec, uint32_t *cnt, cudaStream_t st);
+cudaError_t launch_expand(const ViewParams *views, const float4 *srec, const uint32_t *poff, int64_t n, int64_t P,
+                          float4 *recs, uint32_t *tkey, uint32_t *tval, int *status, cudaStream_t st);
+
+// Depth-ordered render: record gather by sorted index and the ordered splat (tiles up to
+// 32 px; squares of up to 16 px, split when T > 16).
 cudaError_t launch_gather_records(const float4 *src, const uint32_t *idx, int64_t n, float4 *dst, cudaStream_t st);
-cudaError_t launch_widen_index(const int *pid, int64_t n, uint64_t *key, cudaStream_t st);
-cudaError_t launch_gather_keys(const uint64_t *src, const uint32_t *idx, int64_t n, uint64_t *dst, cudaStream_t st);
 int ordered_split(int T);
 int ordered_ctas_per_sm();
 int ordered_workers_per_sm();
 cudaError_t launch_splat_ordered(const SceneDev &sc, const FrameDev &fr, int *queue, float *out,
                                  const float *absorb, float *ord_scratch, int grid, cudaStream_t st);
-cudaError_t radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
-                             int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt);
 size_t splat_smem_bytes(int T);
 cudaError_t launch_selftest_wait(long long limit, int *result, cudaStream_t st);
 cudaError_t launch_final(float *a, int64_t count, cudaStream_t st);

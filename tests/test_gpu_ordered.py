@@ -19,10 +19,12 @@ def _built():
 
 
 def _sorted_on_gpu(keys, vals, lo, hi):
-    k = torch.from_numpy(keys.view(np.int64)).cuda()
+    wide = keys.dtype == np.uint64
+    k = torch.from_numpy(keys.view(np.int64 if wide else np.int32)).cuda()
     v = torch.from_numpy(vals.view(np.int32)).cuda()
-    _lib.check(_lib.load().splotch_debug_sort(k.data_ptr(), v.data_ptr(), keys.shape[0], lo, hi, None), "debug_sort")
-    return k.cpu().numpy().view(np.uint64), v.cpu().numpy().view(np.uint32)
+    _lib.check(_lib.load().splotch_debug_sort(k.data_ptr(), 8 if wide else 4, v.data_ptr(), keys.shape[0], lo, hi,
+                                              None), "debug_sort")
+    return k.cpu().numpy().view(keys.dtype), v.cpu().numpy().view(np.uint32)
 
 
 @pytest.mark.parametrize("n", [2, 7, 4096, 4097, 12289, 1_000_003])
@@ -46,6 +48,23 @@ def test_radix_sort_is_a_stable_sort_by_the_chosen_bits(n):
     k2, v2 = _sorted_on_gpu(k1, v1, 32, 48)
     order = np.lexsort((vals, depth, tile))
     assert np.array_equal(v2, vals[order])
+
+
+@pytest.mark.parametrize("n", [3, 4096, 100_003])
+def test_radix_sort_with_32_bit_keys(n):
+    """The 32-bit-key form the depth-ordered binning uses (particle depth keys, then tile
+    ids): equal to numpy's stable sort by the chosen bits, with ties and an all-ones key."""
+    rng = np.random.default_rng(7 + n)
+    keys = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    keys[rng.random(n) < 0.25] = 0x7F00FF00
+    keys[rng.random(n) < 0.1] = 0xFFFFFFFF
+    vals = np.arange(n, dtype=np.uint32)
+    for lo, hi in ((0, 32), (0, 16), (8, 24), (24, 32)):
+        mask = np.uint32(((1 << (hi - lo)) - 1) << lo)
+        order = np.argsort(keys & mask, kind="stable")
+        k, v = _sorted_on_gpu(keys.copy(), vals.copy(), lo, hi)
+        assert np.array_equal(k, keys[order]), (lo, hi)
+        assert np.array_equal(v, vals[order]), (lo, hi)
 
 
 import oracle  # noqa: E402
