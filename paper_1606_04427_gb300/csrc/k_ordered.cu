@@ -29,8 +29,8 @@ constexpr float kOFar = 1e30f;
 
 struct __align__(16) ORec {
     float X, Y, R2, kr;       // centre, support^2, Gaussian scale (w = 2^(d^2 kr))
-    float kar, kag, kab, inv_s;  // a = 2^(ka w) per channel; 1 / s (0 when s = 0)
-    float e0r, e0g, e0b;      // emission added directly when s = 0 (else 0)
+    float kxr, kxg, kxb, inv_s;  // A = s E per channel (x = A w); 1 / s (0 when s = 0)
+    float er, eg, eb;         // emission E
     uint32_t mask;            // blocks (r * kONC + c) the record's box overlaps
 };
 
@@ -48,6 +48,76 @@ __device__ __forceinline__ int find_tile_o(const int *__restrict__ item_off, int
     }
     return a;
 }
+
+// A record whose largest x = s E w (w <= 1) is at most kSeriesMax takes the series path:
+// phi(x) = (1 - exp(-x)) / x = sum_k (-x)^k / (k + 1)! to degree 5 (next term below
+// x^6 / 7! <= 5e-8 there), a = 1 - x phi, b = E w phi, no exponential per channel.
+constexpr float kSeriesMax = 0.25f;
+constexpr uint32_t kSeriesFlag = 1u << 31;  // in the record's block mask
+
+// Per-lane state: the lane's pixels of block rows 2p and 2p + 1 (same column block c)
+// are held as the two halves of a float2, so that one packed FP32x2 instruction updates
+// both; a pair is computed when either of its two blocks is in the record's mask (a block
+// outside the record's box has no covered pixel, and an uncovered pixel's update is the
+// identity a = 1, b = 0).
+constexpr int kONP = kONR / 2;  // row pairs
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// Apply one record: per pixel and channel I <- a I + b, and the slice map's alpha <- a alpha.
+template <bool kSeries>
+__device__ __forceinline__ void apply_record(const float4 &pa, const float4 &pk, const float4 &pe, uint32_t m,
+                                             const float (&fx)[kONC], const float2 (&fy)[kONP],
+                                             float2 (&al)[kONP][kONC][3], float2 (&be)[kONP][kONC][3]) {
+#pragma unroll
+    for (int q = 0; q < kONP; ++q) {
+        // blocks (2q, c) and (2q + 1, c), c = 0, 1: mask bits 4q .. 4q + 3
+        if (!(m & (0xFu << (4 * q)))) continue;
+        const float2 dy = __fadd2_rn(fy[q], f2(-pa.y));
+        const float2 dy2 = __fmul2_rn(dy, dy);
+#pragma unroll
+        for (int c = 0; c < kONC; ++c) {
+            if (!(m & ((1u << c) | (1u << (kONC + c))) << (4 * q))) continue;
+            const float dx = __fsub_rn(fx[c], pa.x);
+            const float2 d2 = __fadd2_rn(f2(__fmul_rn(dx, dx)), dy2);
+            const float2 e = __fmul2_rn(d2, f2(pa.w));
+            float2 w = make_float2(ex2_fast(e.x), ex2_fast(e.y));
+            w.x = d2.x < pa.z ? w.x : 0.0f;  // uncovered: a = 1, b = 0
+            w.y = d2.y < pa.z ? w.y : 0.0f;
+            const float kx[3] = {pk.x, pk.y, pk.z}, E[3] = {pe.x, pe.y, pe.z};
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float2 x = __fmul2_rn(f2(kx[ch]), w);
+                float2 a, b;
+                if (kSeries) {
+                    float2 phi = __ffma2_rn(x, f2(-1.0f / 720.0f), f2(1.0f / 120.0f));
+                    phi = __ffma2_rn(x, phi, f2(-1.0f / 24.0f));
+                    phi = __ffma2_rn(x, phi, f2(1.0f / 6.0f));
+                    phi = __ffma2_rn(x, phi, f2(-0.5f));
+                    phi = __ffma2_rn(x, phi, f2(1.0f));
+                    a = __ffma2_rn(make_float2(-x.x, -x.y), phi, f2(1.0f));
+                    b = __fmul2_rn(__fmul2_rn(f2(E[ch]), w), phi);
+                } else {
+                    // a = exp(-x), b = (1 - a) / s.  Where x is small, 1 - a in FP32 would
+                    // cancel most digits: there phi to degree 2 (next term x^3 / 24), so
+                    // a = 1 - x phi and b = E w phi (also the s = 0 case)
+                    const float2 phi = __ffma2_rn(x, __ffma2_rn(x, f2(1.0f / 6.0f), f2(-0.5f)), f2(1.0f));
+                    const float2 as = __ffma2_rn(make_float2(-x.x, -x.y), phi, f2(1.0f));
+                    const float2 bs = __fmul2_rn(__fmul2_rn(f2(E[ch]), w), phi);
+                    const float2 ag = make_float2(ex2_fast(x.x * -kLog2e), ex2_fast(x.y * -kLog2e));
+                    const float2 bg = __ffma2_rn(make_float2(-ag.x, -ag.y), f2(pk.w), f2(pk.w));
+                    a = make_float2(x.x < 0.015f ? as.x : ag.x, x.y < 0.015f ? as.y : ag.y);
+                    b = make_float2(x.x < 0.015f ? bs.x : bg.x, x.y < 0.015f ? bs.y : bg.y);
+                }
+                al[q][c][ch] = __fmul2_rn(al[q][c][ch], a);
+                be[q][c][ch] = __ffma2_rn(a, be[q][c][ch], b);
+            }
+        }
+    }
+}
+
+// Element (block row r, column block c, channel ch) of a lane's paired state.
+#define OSTATE(arr, r, c, ch) (((r) & 1) ? arr[(r) >> 1][c][ch].y : arr[(r) >> 1][c][ch].x)
 
 __global__ void __launch_bounds__(kOWarps * 32, 4)
     k_splat_ordered(SceneDev sc, FrameDev fr, int *queue, float *out, int split,
@@ -97,16 +167,19 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
         const int nrec = (tw > 0 && th > 0) ? (int)(min(seg1, e0 + K) - e0) : 0;
         const int nst = (nrec + kOStage - 1) / kOStage;
 
-        float fx[kONC], fy[kONR], al[kONR][kONC][3], be[kONR][kONC][3];
+        float fx[kONC];
+        float2 fy[kONP], al[kONP][kONC][3], be[kONP][kONC][3];
 #pragma unroll
         for (int c = 0; c < kONC; ++c) fx[c] = c * 8 + lc < tw ? (float)(px0 + c * 8 + lc) + 0.5f : kOFar;
 #pragma unroll
-        for (int r = 0; r < kONR; ++r) {
-            fy[r] = r * 4 + lr < th ? (float)(py0 + r * 4 + lr) + 0.5f : kOFar;
+        for (int q = 0; q < kONP; ++q) {
+            const int r0 = 2 * q, r1 = 2 * q + 1;
+            fy[q] = make_float2(r0 * 4 + lr < th ? (float)(py0 + r0 * 4 + lr) + 0.5f : kOFar,
+                                r1 * 4 + lr < th ? (float)(py0 + r1 * 4 + lr) + 0.5f : kOFar);
 #pragma unroll
             for (int c = 0; c < kONC; ++c)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) al[r][c][ch] = 1.0f, be[r][c][ch] = 0.0f;
+                for (int ch = 0; ch < 3; ++ch) al[q][c][ch] = f2(1.0f), be[q][c][ch] = f2(0.0f);
         }
 
         if (lane == 0 && nrec > 0) {
@@ -162,9 +235,9 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
                         const float R2 = __fmul_rn(R, R);
                         float4 *d = reinterpret_cast<float4 *>(&ws->dec[lane]);
                         d[0] = make_float4(X, Y, R2, __fdividef(kexp, R2));
-                        d[1] = make_float4(-s * er * kLog2e, -s * eg * kLog2e, -s * eb * kLog2e, s > 0.0f ? 1.0f / s : 0.0f);
-                        d[2] = make_float4(s > 0.0f ? 0.0f : er, s > 0.0f ? 0.0f : eg, s > 0.0f ? 0.0f : eb,
-                                           __uint_as_float(mask));
+                        d[1] = make_float4(s * er, s * eg, s * eb, s > 0.0f ? 1.0f / s : 0.0f);
+                        const bool series = s * fmaxf(fabsf(er), fmaxf(fabsf(eg), fabsf(eb))) <= kSeriesMax;
+                        d[2] = make_float4(er, eg, eb, __uint_as_float(mask | (series ? kSeriesFlag : 0u)));
                     }
                 }
                 uint32_t live = __ballot_sync(0xffffffffu, mask != 0);
@@ -174,38 +247,13 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
                     const int k = __ffs(live) - 1;
                     live &= live - 1;
                     const float4 pa = *reinterpret_cast<const float4 *>(&ws->dec[k].X);
-                    const float4 pk = *reinterpret_cast<const float4 *>(&ws->dec[k].kar);
-                    const float4 pe = *reinterpret_cast<const float4 *>(&ws->dec[k].e0r);
+                    const float4 pk = *reinterpret_cast<const float4 *>(&ws->dec[k].kxr);
+                    const float4 pe = *reinterpret_cast<const float4 *>(&ws->dec[k].er);
                     const uint32_t m = __float_as_uint(pe.w);
-#pragma unroll
-                    for (int r = 0; r < kONR; ++r) {
-                        if (!(m & (((1u << kONC) - 1u) << (r * kONC)))) continue;
-                        const float dy = __fsub_rn(fy[r], pa.y);
-                        const float dy2 = __fmul_rn(dy, dy);
-#pragma unroll
-                        for (int c = 0; c < kONC; ++c) {
-                            if (!(m & (1u << (r * kONC + c)))) continue;
-                            const float dx = __fsub_rn(fx[c], pa.x);
-                            const float d2 = __fadd_rn(__fmul_rn(dx, dx), dy2);
-                            float w = ex2_fast(d2 * pa.w);
-                            w = d2 < pa.z ? w : 0.0f;  // uncovered: a = 1, b = 0
-                            const float ka[3] = {pk.x, pk.y, pk.z}, e0[3] = {pe.x, pe.y, pe.z};
-#pragma unroll
-                            for (int ch = 0; ch < 3; ++ch) {
-                                // a = exp(-x), x = s E w; 1 - a from its series where x is
-                                // small (1 - a in FP32 would cancel most digits there)
-                                const float t = ka[ch] * w;
-                                const float x = t * -0.69314718f;
-                                const bool small = x < 0.015f;
-                                const float om = small ? x * (1.0f - 0.5f * x * (1.0f - x * (1.0f / 3.0f)))
-                                                       : 1.0f - ex2_fast(t);
-                                const float a = 1.0f - om;
-                                const float b = fmaf(om, pk.w, e0[ch] * w);
-                                al[r][c][ch] *= a;
-                                be[r][c][ch] = fmaf(a, be[r][c][ch], b);
-                            }
-                        }
-                    }
+                    if (m & kSeriesFlag)
+                        apply_record<true>(pa, pk, pe, m, fx, fy, al, be);
+                    else
+                        apply_record<false>(pa, pk, pe, m, fx, fy, al, be);
                 }
                 __syncwarp();
             }
@@ -222,9 +270,9 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
                 for (int c = 0; c < kONC; ++c) {
                     if (c * 8 + lc >= tw) continue;
                     float *p = o + ((int64_t)(py0 + r * 4 + lr) * W + px0 + c * 8 + lc) * 3;
-                    p[0] = be[r][c][0];
-                    p[1] = be[r][c][1];
-                    p[2] = be[r][c][2];
+                    p[0] = OSTATE(be, r, c, 0);
+                    p[1] = OSTATE(be, r, c, 1);
+                    p[2] = OSTATE(be, r, c, 2);
                 }
             }
         } else {
@@ -238,8 +286,8 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
                     const int pix = (qy + r * 4 + lr) * T + qx + c * 8 + lc;
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
-                        map[ch * T * T + pix] = al[r][c][ch];
-                        map[(3 + ch) * T * T + pix] = be[r][c][ch];
+                        map[ch * T * T + pix] = OSTATE(al, r, c, ch);
+                        map[(3 + ch) * T * T + pix] = OSTATE(be, r, c, ch);
                     }
                 }
             }
