@@ -49,11 +49,12 @@ __device__ __forceinline__ int find_tile_o(const int *__restrict__ item_off, int
     return a;
 }
 
-// A record whose largest x = s E w (w <= 1) is at most kSeriesMax takes the series path:
-// phi(x) = (1 - exp(-x)) / x = sum_k (-x)^k / (k + 1)! to degree 5 (next term below
-// x^6 / 7! <= 5e-8 there), a = 1 - x phi, b = E w phi, no exponential per channel.
-constexpr float kSeriesMax = 0.25f;
-constexpr uint32_t kSeriesFlag = 1u << 31;  // in the record's block mask
+// A record whose largest x = s E w (w <= 1) is small takes a series path: with
+// phi(x) = (1 - exp(-x)) / x = sum_k (-x)^k / (k + 1)!, a = 1 - x phi and b = E w phi, no
+// exponential per channel.  phi to degree 2 where x <= kSeries2Max (next term x^3 / 24
+// <= 1.5e-7 relative), to degree 5 where x <= kSeries5Max (x^6 / 7! <= 5e-8).
+constexpr float kSeries2Max = 0.015f, kSeries5Max = 0.25f;
+constexpr uint32_t kSeries5Flag = 1u << 31, kSeries2Flag = 1u << 30;  // in the record's block mask
 
 // Per-lane state: the lane's pixels of block rows 2p and 2p + 1 (same column block c)
 // are held as the two halves of a float2, so that one packed FP32x2 instruction updates
@@ -65,7 +66,7 @@ constexpr int kONP = kONR / 2;  // row pairs
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
 // Apply one record: per pixel and channel I <- a I + b, and the slice map's alpha <- a alpha.
-template <bool kSeries>
+template <int kDeg>  // 2 or 5: series of that degree; 0: exponential
 __device__ __forceinline__ void apply_record(const float4 &pa, const float4 &pk, const float4 &pe, uint32_t m,
                                              const float (&fx)[kONC], const float2 (&fy)[kONP],
                                              float2 (&al)[kONP][kONC][3], float2 (&be)[kONP][kONC][3]) {
@@ -89,10 +90,15 @@ __device__ __forceinline__ void apply_record(const float4 &pa, const float4 &pk,
             for (int ch = 0; ch < 3; ++ch) {
                 const float2 x = __fmul2_rn(f2(kx[ch]), w);
                 float2 a, b;
-                if (kSeries) {
-                    float2 phi = __ffma2_rn(x, f2(-1.0f / 720.0f), f2(1.0f / 120.0f));
-                    phi = __ffma2_rn(x, phi, f2(-1.0f / 24.0f));
-                    phi = __ffma2_rn(x, phi, f2(1.0f / 6.0f));
+                if (kDeg > 0) {
+                    float2 phi;
+                    if (kDeg == 5) {
+                        phi = __ffma2_rn(x, f2(-1.0f / 720.0f), f2(1.0f / 120.0f));
+                        phi = __ffma2_rn(x, phi, f2(-1.0f / 24.0f));
+                        phi = __ffma2_rn(x, phi, f2(1.0f / 6.0f));
+                    } else {
+                        phi = f2(1.0f / 6.0f);
+                    }
                     phi = __ffma2_rn(x, phi, f2(-0.5f));
                     phi = __ffma2_rn(x, phi, f2(1.0f));
                     a = __ffma2_rn(make_float2(-x.x, -x.y), phi, f2(1.0f));
@@ -236,8 +242,9 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
                         float4 *d = reinterpret_cast<float4 *>(&ws->dec[lane]);
                         d[0] = make_float4(X, Y, R2, __fdividef(kexp, R2));
                         d[1] = make_float4(s * er, s * eg, s * eb, s > 0.0f ? 1.0f / s : 0.0f);
-                        const bool series = s * fmaxf(fabsf(er), fmaxf(fabsf(eg), fabsf(eb))) <= kSeriesMax;
-                        d[2] = make_float4(er, eg, eb, __uint_as_float(mask | (series ? kSeriesFlag : 0u)));
+                        const float xmax = s * fmaxf(fabsf(er), fmaxf(fabsf(eg), fabsf(eb)));
+                        const uint32_t path = xmax <= kSeries2Max ? kSeries2Flag : (xmax <= kSeries5Max ? kSeries5Flag : 0u);
+                        d[2] = make_float4(er, eg, eb, __uint_as_float(mask | path));
                     }
                 }
                 uint32_t live = __ballot_sync(0xffffffffu, mask != 0);
@@ -250,10 +257,12 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
                     const float4 pk = *reinterpret_cast<const float4 *>(&ws->dec[k].kxr);
                     const float4 pe = *reinterpret_cast<const float4 *>(&ws->dec[k].er);
                     const uint32_t m = __float_as_uint(pe.w);
-                    if (m & kSeriesFlag)
-                        apply_record<true>(pa, pk, pe, m, fx, fy, al, be);
+                    if (m & kSeries2Flag)
+                        apply_record<2>(pa, pk, pe, m, fx, fy, al, be);
+                    else if (m & kSeries5Flag)
+                        apply_record<5>(pa, pk, pe, m, fx, fy, al, be);
                     else
-                        apply_record<false>(pa, pk, pe, m, fx, fy, al, be);
+                        apply_record<0>(pa, pk, pe, m, fx, fy, al, be);
                 }
                 __syncwarp();
             }

@@ -107,6 +107,19 @@ def test_ordered_matches_the_depth_ordered_oracle(tile):
     assert np.abs(ref - oracle.final(oracle.render(ps, cam))).max() > 1e-2
 
 
+@pytest.mark.parametrize("absorb", [[0.1, 0.02], [2.0, 0.3], [8.0, 3.0]])
+def test_ordered_each_transfer_path_matches_the_oracle(absorb):
+    """The splat picks, per record, the degree-2 series (largest x = s E below 0.015), the
+    degree-5 series (up to 0.25) or the exponential; these absorptions put the records of
+    the scene (emission up to 0.05 and 0.3) on each path in turn."""
+    ps = _species_set(44)
+    cam = synth.front_camera(176, 144)
+    ref = oracle.render_rt_depth(ps, cam, absorb)
+    got = render.Scene(ps, "f32").render_ordered(cam, absorb, render.RenderParams(tile=16)).cpu().numpy()
+    err = float(np.abs(got - ref).max())
+    assert err <= TOL_O["f32"], (absorb, err)
+
+
 def test_ordered_split_tiles_compose_their_slices():
     """A crowded tile is cut into slices of the depth-sorted list; the slices' affine maps
     compose far to near.  Also zero absorption (additive species) and FP16 storage."""
