@@ -51,7 +51,7 @@ def _bind(path: str):
     lib = C.CDLL(path)
     P = C.c_void_p
     i64, i32, f32, f64 = C.c_int64, C.c_int, C.c_float, C.c_double
-    scene = [i64, P, P, P, P, P, i32, P, P, P, P, P, P, i32, i32, f32, f32, f64]
+    scene = [i64, P, P, P, P, P, i32, P, P, P, P, P, P, i32, i32, f32, f32, f64, P, P]
     lib.orc_camera.argtypes = [P, P, P, f64, f64, i32, i32, P, P]
     lib.orc_camera.restype = i32
     lib.orc_normalise.argtypes = [i64, P, i32, i32, f64, f64, i32, P]
@@ -201,6 +201,31 @@ def normalise(ps, storage: str = "f32") -> np.ndarray:
     return out
 
 
+def normalise_rgb(ps):
+    """Normalised colour components (n x 3, FP64) of the vector-coloured species, zeros
+    elsewhere; None when the set has no vector-coloured species.  A species' three
+    components share one range (given, or their joint min / max) and its log flag."""
+    vec = getattr(ps, "col_vector", None)
+    if vec is None or not np.any(np.asarray(vec)):
+        return None
+    lib = _cur()
+    n = int(ps.x.shape[0])
+    out = np.zeros((n, 3), np.float64)
+    tb = np.asarray(ps.type_begin, np.int64)
+    for t in range(tb.shape[0] - 1):
+        if not vec[t]:
+            continue
+        s, e = int(tb[t]), int(tb[t + 1])
+        comp = np.ascontiguousarray(ps.rgb[s:e], np.float32).reshape(-1)
+        seg = np.empty(comp.shape[0], np.float64)
+        given = ps.i_min is not None and ps.i_max is not None
+        lo = float(ps.i_min[t]) if given else 0.0
+        hi = float(ps.i_max[t]) if given else 0.0
+        lib.orc_normalise(comp.shape[0], _ptr(comp), int(ps.i_log[t]), int(given), lo, hi, 0, _ptr(seg))
+        out[s:e] = seg.reshape(-1, 3)
+    return out
+
+
 class _Scene:
     """Keeps the marshalled arrays alive for one oracle call."""
 
@@ -219,13 +244,16 @@ class _Scene:
         self.m, self.p = camera(cam)
         self.W, self.H = int(cam.width), int(cam.height)
         self.params = params
+        self.rgb = normalise_rgb(ps)
+        self.vec = (np.ascontiguousarray(ps.col_vector, np.int32) if self.rgb is not None else None)
 
     def args(self):
         pr = self.params
         return [self.n, _ptr(self.x), _ptr(self.y), _ptr(self.z), _ptr(self.h), _ptr(self.It),
                 self.nt, _ptr(self.tb), C.cast(self.cm_ptrs, C.c_void_p), _ptr(self.cm_len),
                 _ptr(self.beta), _ptr(self.m), _ptr(self.p), self.W, self.H,
-                float(pr.rfac), float(pr.r_min_px), float(pr.sigma_over_R)]
+                float(pr.rfac), float(pr.r_min_px), float(pr.sigma_over_R),
+                None if self.rgb is None else _ptr(self.rgb), None if self.vec is None else _ptr(self.vec)]
 
 
 def raster(ps, cam, params: Params = Params(), storage: str = "f32"):

@@ -262,6 +262,14 @@ static void colour(double It, const float *cmap, int n, double beta, double e[3]
         e[c] = beta * ((1.0 - tau) * (double)cmap[3 * k + c] + tau * (double)cmap[3 * (k + 1) + c]);
 }
 
+/* Colour directly from a vector input field (Section 2.1: the RGB triple of a particle,
+ * its three components ranged and normalised like a scalar, one range per species):
+ *   e = beta (r~, g~, b~).   FP64. */
+static void colour_vector(const double rgb[3], double beta, double e[3])
+{
+    for (int c = 0; c < 3; ++c) e[c] = beta * rgb[c];
+}
+
 /* Gaussian weight, sigma = sigma_over_R * R, FP64 distance from the FP32 centre. */
 static double weight(const orc_px *o, int i, int j, double sor)
 {
@@ -289,6 +297,8 @@ typedef struct {
     int W, H;
     float rfac, rmin;
     double sor;
+    const double *rgb;  /* n x 3 normalised colour components, or NULL */
+    const int *vec;     /* per species: 1 = colour from rgb, or NULL (all from the colormap) */
 } orc_scene;
 
 static int type_of(const orc_scene *s, int64_t i)
@@ -307,7 +317,10 @@ static orc_px *raster_all(const orc_scene *s, double (*ecol)[3])
         raster_one(s->x[i], s->y[i], s->z[i], s->h[i], s->m, s->p, s->W, s->H, s->rfac, s->rmin, &px[i]);
         if (ecol) {
             int t = type_of(s, i);
-            colour(s->It[i], s->cmap[t], s->cmap_len[t], s->beta[t], ecol[i]);
+            if (s->vec && s->vec[t])
+                colour_vector(&s->rgb[3 * i], s->beta[t], ecol[i]);
+            else
+                colour(s->It[i], s->cmap[t], s->cmap_len[t], s->beta[t], ecol[i]);
         }
     }
     return px;
@@ -317,8 +330,10 @@ static void fill_scene(orc_scene *s, int64_t n, const float *x, const float *y, 
                        const float *h, const double *It, int n_types, const int64_t *type_begin,
                        const float *const *cmap, const int *cmap_len, const double *beta,
                        const float m[12], const float p[4], int W, int H, float rfac, float rmin,
-                       double sor)
+                       double sor, const double *rgb, const int *vec)
 {
+    s->rgb = rgb;
+    s->vec = vec;
     s->n = n;
     s->x = x; s->y = y; s->z = z; s->h = h;
     s->It = It;
@@ -337,8 +352,8 @@ static void fill_scene(orc_scene *s, int64_t n, const float *x, const float *y, 
     int64_t n, const float *x, const float *y, const float *z, const float *h, const double *It,   \
         int n_types, const int64_t *type_begin, const float *const *cmap, const int *cmap_len,     \
         const double *beta, const float m[12], const float p[4], int W, int H, float rfac,         \
-        float rmin, double sor
-#define SCENE_PASS n, x, y, z, h, It, n_types, type_begin, cmap, cmap_len, beta, m, p, W, H, rfac, rmin, sor
+        float rmin, double sor, const double *rgb, const int *vec
+#define SCENE_PASS n, x, y, z, h, It, n_types, type_begin, cmap, cmap_len, beta, m, p, W, H, rfac, rmin, sor, rgb, vec
 
 /* Per-particle raster outputs: X, Y, R, zc, e_r, e_g, e_b (FP64) and the active flag. */
 int orc_raster(SCENE_ARGS, double *out7, int32_t *active, int32_t *box4)

@@ -53,6 +53,10 @@ class ParticleSet:
     i_min: Optional[np.ndarray] = None
     i_max: Optional[np.ndarray] = None
     name: str = ""
+    # colour from a vector field: per-particle RGB (n x 3, FP32) used by the species whose
+    # col_vector entry is nonzero (the others keep intensity -> colormap)
+    rgb: Optional[np.ndarray] = None
+    col_vector: Optional[np.ndarray] = None
 
     @property
     def n(self) -> int:
@@ -71,7 +75,9 @@ class ParticleSet:
                            self.i_log.copy(),
                            None if self.i_min is None else self.i_min.copy(),
                            None if self.i_max is None else self.i_max.copy(),
-                           self.name)
+                           self.name,
+                           None if self.rgb is None else self.rgb[idx],
+                           None if self.col_vector is None else self.col_vector.copy())
 
     def with_brightness(self, beta: Sequence[float]) -> "ParticleSet":
         out = ParticleSet(**{k: getattr(self, k) for k in self.__dataclass_fields__})

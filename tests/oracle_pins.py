@@ -485,6 +485,57 @@ def pin_rt_depth_lattice_is_the_full_image_restricted():
 # ----------------------------------------------------------------------------------------
 # colour (Section 2.1: scalar through a runtime colormap) and preprocessing
 
+def _vector_set(rgb, n_scalar=0, i_log=(0, 0), i_min=None, i_max=None, beta=(0.7, 1.3)):
+    """n_scalar colormap particles (species 0) then len(rgb) vector-coloured ones
+    (species 1), all at the image centre."""
+    n = n_scalar + len(rgb)
+    ps = make_set([0.5] * n, [0.5] * n, [0.5] * n, [0.01] * n, np.linspace(0.0, 1.0, n),
+                  type_begin=[0, n_scalar, n], betas=list(beta))
+    ps.i_log = np.asarray(i_log, np.int32)
+    ps.i_min = None if i_min is None else np.asarray(i_min, np.float32)
+    ps.i_max = None if i_max is None else np.asarray(i_max, np.float32)
+    full = np.zeros((n, 3), np.float32)
+    full[n_scalar:] = np.asarray(rgb, np.float32)
+    ps.rgb, ps.col_vector = full, np.array([0, 1], np.int32)
+    return ps
+
+
+def pin_vector_colour_is_the_ranged_rgb_triple():
+    """Colour from a vector field: e = brightness x (C - lo) / (hi - lo) per component,
+    one range over the species' three components (here r spans [0, 2], g [0, 1], b
+    [0.5, 1]: a per-component range would give other values); the scalar species keeps
+    its colormap colour."""
+    rgb = [[0.0, 1.0, 0.5], [2.0, 0.25, 1.0], [1.0, 0.0, 0.75]]
+    ps = _vector_set(rgb, n_scalar=2)
+    e = oracle.raster(ps, front(16, 16))["e"]
+    want = 1.3 * np.asarray(rgb, np.float64) / 2.0
+    assert np.allclose(e[2:], want, rtol=0, atol=1e-7), e[2:]
+    plain = ps.subset(np.arange(2))
+    plain.rgb, plain.col_vector = None, None
+    assert np.array_equal(e[:2], oracle.raster(plain, front(16, 16))["e"])
+    # given range with clamping, and the log flag
+    ps = _vector_set(rgb, i_min=[0.0, 0.5], i_max=[1.0, 1.5])
+    e = oracle.raster(ps, front(16, 16))["e"]
+    assert np.allclose(e, 1.3 * np.clip((np.asarray(rgb) - 0.5) / 1.0, 0, 1), rtol=0, atol=1e-7)
+    rgb2 = [[1.0, np.e, np.e ** 2], [np.e ** 4, 1.0, np.e]]
+    ps = _vector_set(rgb2, i_log=(0, 1))
+    e = oracle.raster(ps, front(16, 16))["e"]
+    assert np.allclose(e, 1.3 * np.log(np.asarray(rgb2, np.float32).astype(np.float64)) / 4.0, rtol=0,
+                       atol=1e-6)
+
+
+def pin_vector_colour_peak_pixel():
+    """One vector-coloured particle centred on a pixel centre deposits exactly its
+    emission there (weight 1), channel by channel."""
+    W = H = 64
+    X, Y = 20.5, 33.5
+    pt = world_for_screen(X, Y, W, H, depth=2.0)
+    ps = make_set([pt[0]], [pt[1]], [pt[2]], [(4.0 / 0.75) * 2.0 / focal(H)], [0.5], beta=0.9)
+    ps.rgb, ps.col_vector = np.array([[0.2, 0.9, 0.5]], np.float32), np.array([1], np.int32)
+    ps.i_min, ps.i_max = np.array([0.0], np.float32), np.array([1.0], np.float32)
+    a = oracle.render(ps, front(W, H))
+    assert np.allclose(a[33, 20], 0.9 * np.array([0.2, 0.9, 0.5]), rtol=0, atol=1e-7), a[33, 20]
+
 def pin_colormap_special_values():
     cm = np.array([[0.0, 0.1, 0.2], [0.3, 0.5, 0.7], [1.0, 0.0, 0.5], [0.2, 0.9, 0.4],
                    [0.6, 0.6, 0.6]], np.float32)

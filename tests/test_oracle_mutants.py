@@ -40,6 +40,9 @@ MUTANTS = {
     "rt_depth_one_species": ("const double st = absorb[type_of(&s, k)];", "const double st = absorb[0];"),
     "rt_depth_emission_over_absorption_dropped": ("v[c] = v[c] * t + (E / A) * (1.0 - t);",
                                                   "v[c] = v[c] * t + (1.0 - t);"),
+    "vector_colour_ignored": ("if (s->vec && s->vec[t])", "if (0 && s->vec)"),
+    "vector_components_swapped": ("for (int c = 0; c < 3; ++c) e[c] = beta * rgb[c];",
+                                  "for (int c = 0; c < 3; ++c) e[c] = beta * rgb[2 - c];"),
     "image_transposed": ("double *q = &a[3 * ((size_t)j * W + i)];\n                    for (int c = 0; c < 3; ++c) q[c] += e[k][c] * w;",
                          "double *q = &a[3 * ((size_t)(i % H) * W + (j % W))];\n                    for (int c = 0; c < 3; ++c) q[c] += e[k][c] * w;"),
     "final_wrong": ("O[i] = -expm1(-a[i]);", "O[i] = 1.0 - exp(-2.0 * a[i]);"),
