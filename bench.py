@@ -50,6 +50,13 @@ def make_workload(name: str):
         cam = synth.front_camera(2048, 2048)
         storage = "f16" if name.endswith("f16") else "f32"
         b = beta.get("two_species", [1.0, 1.0])
+    elif name == "two_species_vector_f16":
+        # the same frame with the stars coloured from a per-particle RGB field
+        ps = _cached(cache, "two_species", lambda: synth.two_species_set(70_000_000, 30_000_000, 2))
+        ps = synth.with_vector_colour(ps, [1], 2)
+        cam = synth.front_camera(2048, 2048)
+        storage = "f16"
+        b = beta.get("two_species", [1.0, 1.0])
     elif name == "two_species_small":
         ps = _cached(cache, "two_species_small", lambda: synth.two_species_set(7_000_000, 3_000_000, 2))
         cam = synth.front_camera(2048, 2048)
@@ -178,6 +185,8 @@ def work_units(name):
     p = os.path.join(ROOT, "tests", "golden", "work_units.json")
     if not os.path.exists(p):
         return None
+    # the vector-colour frame has the geometry (particles, camera) of the plain one
+    name = {"two_species_vector_f16": "two_species_f16"}.get(name, name)
     with open(p) as f:
         return json.load(f).get(name)
 

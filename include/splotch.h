@@ -101,6 +101,19 @@ typedef struct {
     const int32_t *i_log;
     splotch_allocator allocator;
     void *stream;
+    /* Colour from a vector field (Section 2.1: colours come directly from a vector input
+     * field, or from a scalar through a colormap).  col_vector: NULL (every species uses
+     * its colormap), or host, per type: nonzero = the species' colour is the particle's RGB
+     * triple.  rgb: n x 3 floats (r, g, b interleaved), where on_device says (host input
+     * may be pageable or page-locked); read for the particles of vector-coloured species,
+     * which must be finite, and ignored elsewhere.  A vector species' components are
+     * ranged and normalised like the intensity, with its i_log and one range over its
+     * three components (i_min / i_max, or their joint min / max): emission = brightness x
+     * (r~, g~, b~); its intensity is not used.  The scene then holds a per-particle FP32
+     * emission (16 bytes per particle, whatever the storage) and its tile records carry
+     * particle indices. */
+    const int32_t *col_vector;
+    const float *rgb;
 } splotch_scene_desc;
 
 /* Camera (Section 2.1: supplied camera and look-at positions).  FP64 on the host; the

@@ -31,7 +31,8 @@ class SceneDesc(C.Structure):
                 ("intensity", C.c_void_p), ("on_device", C.c_int32), ("storage", C.c_int32),
                 ("cmap_rgb", C.c_void_p), ("cmap_len", C.c_void_p), ("brightness", C.c_void_p),
                 ("i_min", C.c_void_p), ("i_max", C.c_void_p), ("i_log", C.c_void_p),
-                ("allocator", Allocator), ("stream", C.c_void_p)]
+                ("allocator", Allocator), ("stream", C.c_void_p),
+                ("col_vector", C.c_void_p), ("rgb", C.c_void_p)]
 
 
 class CameraC(C.Structure):

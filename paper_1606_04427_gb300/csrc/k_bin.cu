@@ -181,6 +181,61 @@ static void prepare_launch(const float *x, const float *y, const float *z, const
     }
 }
 
+// Per-particle emission of a scene with vector-coloured species (Section 2.1: colour
+// directly from a vector input field, or from a scalar through the colormap): for a
+// vector species, C~ = clamp((C' - lo) / (hi - lo), 0, 1) per component (C' = ln(max(C,
+// 1e-30)) with the log flag; 0 when hi <= lo) and e = brightness C~; for the others the
+// colormap (premultiplied by brightness) interpolated at the stored normalised intensity.
+// The species index rides in .w.  A non-finite colour component sets *bad.
+template <int S>
+__global__ void k_emission(SceneDev sc, const float *__restrict__ rgb, const int *__restrict__ vec,
+                           const float *__restrict__ lo, const float *__restrict__ hi, const int *__restrict__ lg,
+                           const float *__restrict__ beta, float4 *emit, int *bad) {
+    __shared__ int64_t s_tb[kMaxTypes + 1];
+    for (int k = threadIdx.x; k <= sc.n_types; k += blockDim.x) s_tb[k] = sc.type_begin[k];
+    __syncthreads();
+    int type = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sc.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
+        float e[3];
+        if (vec[type]) {
+            const float l = lo[type], span = hi[type] - l;
+            for (int c = 0; c < 3; ++c) {
+                float v = rgb[3 * i + c];
+                if (!isfinite(v)) atomicExch(bad, 1);
+                if (lg[type]) v = logf(fmaxf(v, 1e-30f));
+                float t = span > 0.0f ? (v - l) / span : 0.0f;
+                t = fminf(fmaxf(t, 0.0f), 1.0f);
+                e[c] = beta[type] * t;
+            }
+        } else {
+            const float It = load1<S>(sc.it, i);
+            const int len = sc.lut_len[type];
+            const float f = It * (float)(len - 1);
+            const int kk = min((int)f, len - 2);
+            const float tau = f - (float)kk;
+            const float4 c0 = sc.lut[sc.lut_off[type] + kk], c1 = sc.lut[sc.lut_off[type] + kk + 1];
+            e[0] = (1.0f - tau) * c0.x + tau * c1.x;
+            e[1] = (1.0f - tau) * c0.y + tau * c1.y;
+            e[2] = (1.0f - tau) * c0.z + tau * c1.z;
+        }
+        emit[i] = make_float4(e[0], e[1], e[2], __int_as_float(type));
+    }
+}
+
+cudaError_t launch_emission(int storage, const SceneDev &sc, const float *rgb, const int *vec, const float *lo,
+                            const float *hi, const int *lg, const float *beta, float4 *emit, int *bad,
+                            cudaStream_t st) {
+    if (sc.n <= 0) return cudaSuccess;
+    int64_t blocks = (sc.n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (storage == 0) k_emission<0><<<(int)blocks, 256, 0, st>>>(sc, rgb, vec, lo, hi, lg, beta, emit, bad);
+    else if (storage == 1) k_emission<1><<<(int)blocks, 256, 0, st>>>(sc, rgb, vec, lo, hi, lg, beta, emit, bad);
+    else k_emission<2><<<(int)blocks, 256, 0, st>>>(sc, rgb, vec, lo, hi, lg, beta, emit, bad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prepare(const float *x, const float *y, const float *z, const float *h,
                            const float *I, int64_t n, int n_types, const int64_t *type_begin,
                            const float *lo, const float *hi, const int *i_log, int storage,
@@ -444,7 +499,8 @@ cudaError_t launch_scan(const FrameDev &fr, int target_items, int kmin, cudaStre
 
 // ---------------------------------------------------------------------------------------
 // k_scatter: same chunks as k_count; every (particle, tile) pair becomes a record
-// {X, Y, R, type << 24 | 24-bit normalised intensity} in its tile segment.
+// {X, Y, R, type << 24 | 24-bit normalised intensity} in its tile segment (in scenes with
+// a per-particle emission the last word is the particle index).
 
 // Write the records of one particle for every view of the group (same split between
 // lane and warp as count_particle).  Called by all lanes of the warp together.
@@ -562,8 +618,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
     for (; i - lane < e; i += 2 * stride) {
         if (i < e)
             while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
-        scatter_particle(i < e, i, ax, ay, az, ah, record_code(type, ai), s_view, s_vbase, g_n, s_cur, nt, fr,
-                         lane);
+        scatter_particle(i < e, i, ax, ay, az, ah, sc.emit ? __uint_as_float((uint32_t)i) : record_code(type, ai),
+                         s_view, s_vbase, g_n, s_cur, nt, fr, lane);
         const int64_t ia = i + 2 * stride;
         if (ia < e)
             ax = load1<S>(sc.x, ia), ay = load1<S>(sc.y, ia), az = load1<S>(sc.z, ia), ah = load1<S>(sc.h, ia),
@@ -572,8 +628,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
         if (j - lane >= e) break;
         if (j < e)
             while (type + 1 < sc.n_types && j >= s_tb[type + 1]) ++type;
-        scatter_particle(j < e, j, bx, by, bz, bh, record_code(type, bi), s_view, s_vbase, g_n, s_cur, nt, fr,
-                         lane);
+        scatter_particle(j < e, j, bx, by, bz, bh, sc.emit ? __uint_as_float((uint32_t)j) : record_code(type, bi),
+                         s_view, s_vbase, g_n, s_cur, nt, fr, lane);
         const int64_t ib = i + 3 * stride;
         if (ib < e)
             bx = load1<S>(sc.x, ib), by = load1<S>(sc.y, ib), bz = load1<S>(sc.z, ib), bh = load1<S>(sc.h, ib),
@@ -697,7 +753,8 @@ __global__ void __launch_bounds__(256) k_depth_records(SceneDev sc, const ViewPa
         Raster r;
         const bool act = raster_one(s_v, load1<S>(sc.x, i), load1<S>(sc.y, i), load1<S>(sc.z, i),
                                     load1<S>(sc.h, i), r);
-        prec[i] = make_float4(r.X, r.Y, r.R, record_code(type, load1<S>(sc.it, i)));
+        prec[i] = make_float4(r.X, r.Y, r.R,
+                              sc.emit ? __uint_as_float((uint32_t)i) : record_code(type, load1<S>(sc.it, i)));
         dkey[i] = act ? (uint32_t)depth_key(r.zc) : kInactiveKey;
         pid[i] = (uint32_t)i;
     }

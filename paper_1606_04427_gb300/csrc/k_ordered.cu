@@ -226,17 +226,26 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
                     if (ilo <= ihi && jlo <= jhi) {
                         const uint32_t cm = (2u << (ihi >> 3)) - (1u << (ilo >> 3));
                         for (int r = jlo >> 2; r <= (jhi >> 2); ++r) mask |= cm << (r * kONC);
-                        const int type = (int)(code >> 24);
-                        const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
-                        const int len = __ldg(&sc.lut_len[type]);
-                        const float f = It * (float)(len - 1);
-                        const int kk = min((int)f, len - 2);
-                        const float tau = f - (float)kk;
-                        const int lo = __ldg(&sc.lut_off[type]) + kk;
-                        const float4 c0 = __ldg(&sc.lut[lo]);
-                        const float4 c1 = __ldg(&sc.lut[lo + 1]);
-                        const float er = (1.0f - tau) * c0.x + tau * c1.x, eg = (1.0f - tau) * c0.y + tau * c1.y;
-                        const float eb = (1.0f - tau) * c0.z + tau * c1.z;
+                        int type;
+                        float er, eg, eb;
+                        if (sc.emit) {
+                            const float4 em = __ldg(&sc.emit[code]);  // the code is the particle index
+                            type = __float_as_int(em.w);
+                            er = em.x, eg = em.y, eb = em.z;
+                        } else {
+                            type = (int)(code >> 24);
+                            const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
+                            const int len = __ldg(&sc.lut_len[type]);
+                            const float f = It * (float)(len - 1);
+                            const int kk = min((int)f, len - 2);
+                            const float tau = f - (float)kk;
+                            const int lo = __ldg(&sc.lut_off[type]) + kk;
+                            const float4 c0 = __ldg(&sc.lut[lo]);
+                            const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                            er = (1.0f - tau) * c0.x + tau * c1.x;
+                            eg = (1.0f - tau) * c0.y + tau * c1.y;
+                            eb = (1.0f - tau) * c0.z + tau * c1.z;
+                        }
                         const float s = __ldg(&absorb[type]);
                         const float R2 = __fmul_rn(R, R);
                         float4 *d = reinterpret_cast<float4 *>(&ws->dec[lane]);

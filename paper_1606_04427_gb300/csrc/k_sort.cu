@@ -127,12 +127,18 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const K *__restr
                                                                const uint32_t *__restrict__ offs,
                                                                K *keys_out, uint32_t *vals_out) {
     __shared__ uint32_t s_wc[kSortWarps][256];  // per warp: running count, then warp base
-    __shared__ uint32_t s_off[256];
+    __shared__ uint32_t s_off[256];             // output start of this CTA's digit d
+    __shared__ uint32_t s_loc[256];             // start of digit d in the CTA's staged tile
+    __shared__ uint32_t s_scan[33];
+    __shared__ __align__(16) K s_key[kSortTile];  // staged keys, then staged values
+    __shared__ uint8_t s_dig[kSortTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < kSortWarps * 256; k += kSortThreads) (&s_wc[0][0])[k] = 0;
     for (int d = threadIdx.x; d < 256; d += kSortThreads) s_off[d] = offs[(int64_t)d * n_blocks + blockIdx.x];
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kSortPerWarp;
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int cnt = (int)min((int64_t)kSortTile, n - tile0);
+    const int64_t base = tile0 + (int64_t)warp * kSortPerWarp;
     K k_r[kSortRounds];
     uint32_t v_r[kSortRounds], rank[kSortRounds];
     const uint32_t lt = (1u << lane) - 1u;
@@ -156,24 +162,65 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const K *__restr
         __syncwarp();  // this round's counter updates before the next round reads them
     }
     __syncthreads();
-    // warp bases: elements of earlier warps with the same digit come first
-    for (int d = threadIdx.x; d < 256; d += kSortThreads) {
+    // warp bases (elements of earlier warps with the same digit come first), the CTA's
+    // digit totals, and their exclusive scan: where each digit starts in the staged tile
+    {
+        const int d = threadIdx.x;  // kSortThreads == 256 digits
         uint32_t run = 0;
         for (int w = 0; w < kSortWarps; ++w) {
             const uint32_t c = s_wc[w][d];
             s_wc[w][d] = run;
             run += c;
         }
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_scan[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t wv = lane < kSortWarps ? s_scan[lane] : 0u;
+            uint32_t wi = wv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += u;
+            }
+            if (lane < kSortWarps) s_scan[lane] = wi - wv;
+        }
+        __syncthreads();
+        s_loc[d] = s_scan[warp] + incl - run;
     }
     __syncthreads();
+    // stage the keys in digit order, then write each digit's run to consecutive slots
+    uint32_t loc[kSortRounds];
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
         const int64_t i = base + r * 32 + lane;
         if (i >= n) continue;
         const uint32_t d = digit_of(k_r[r], shift);
-        const uint32_t pos = s_off[d] + s_wc[warp][d] + rank[r];
-        keys_out[pos] = k_r[r];
-        vals_out[pos] = v_r[r];
+        loc[r] = s_loc[d] + s_wc[warp][d] + rank[r];
+        s_key[loc[r]] = k_r[r];
+        s_dig[loc[r]] = (uint8_t)d;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < cnt; l += kSortThreads) {
+        const uint32_t d = s_dig[l];
+        keys_out[s_off[d] + (uint32_t)l - s_loc[d]] = s_key[l];
+    }
+    __syncthreads();
+    uint32_t *s_val = reinterpret_cast<uint32_t *>(s_key);
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        if (i < n) s_val[loc[r]] = v_r[r];
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < cnt; l += kSortThreads) {
+        const uint32_t d = s_dig[l];
+        vals_out[s_off[d] + (uint32_t)l - s_loc[d]] = s_val[l];
     }
 }
 

@@ -27,8 +27,9 @@ namespace spl {
 // ---------------------------------------------------------------------------------------
 // CTA-per-item splat for tiles above 32 px.  Per stage of kStage records:
 //   1. decode: one thread per record computes the record's pixel box inside the tile, its
-//      colour (brightness x colormap) and Gaussian scale, and appends the record to the
-//      list of every warp owning a block row the box meets (block row r: warp r mod 8);
+//      colour (brightness x colormap, or the particle's emission) and Gaussian scale, and
+//      appends the record to the list of every warp owning a block row the box meets
+//      (block row r: warp r mod 8);
 //   2. gather: each warp walks its list; for every block of its own that the box
 //      overlaps, each lane tests its pixel with the FP32 coverage rule and adds e * w
 //      to its registers.
@@ -171,15 +172,25 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 const int jlo = max(py0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))));
                 const int jhi = min(py0 + th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))));
                 if (ilo > ihi || jlo > jhi) continue;
-                const int type = (int)(code >> 24);
-                const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
-                const int len = __ldg(&sc.lut_len[type]);
-                const float f = It * (float)(len - 1);
-                const int kk = min((int)f, len - 2);
-                const float tau = f - (float)kk;
-                const int lo = __ldg(&sc.lut_off[type]) + kk;
-                const float4 c0 = __ldg(&sc.lut[lo]);
-                const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                int type;
+                float3 e;
+                if (sc.emit) {
+                    const float4 em = __ldg(&sc.emit[code]);  // the code is the particle index
+                    type = __float_as_int(em.w);
+                    e = make_float3(em.x, em.y, em.z);
+                } else {
+                    type = (int)(code >> 24);
+                    const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
+                    const int len = __ldg(&sc.lut_len[type]);
+                    const float f = It * (float)(len - 1);
+                    const int kk = min((int)f, len - 2);
+                    const float tau = f - (float)kk;
+                    const int lo = __ldg(&sc.lut_off[type]) + kk;
+                    const float4 c0 = __ldg(&sc.lut[lo]);
+                    const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                    e = make_float3((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
+                                    (1.0f - tau) * c0.z + tau * c1.z);
+                }
                 Rec q;
                 q.ilo = ilo - px0;
                 q.ihi = ihi - px0;
@@ -190,9 +201,9 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 q.R2 = __fmul_rn(R, R);
                 q.kr = __fdividef(kexp, q.R2);
                 const float vs = fr.vscale ? __ldg(&fr.vscale[v * sc.n_types + type]) : 1.0f;
-                q.er = ((1.0f - tau) * c0.x + tau * c1.x) * vs;
-                q.eg = ((1.0f - tau) * c0.y + tau * c1.y) * vs;
-                q.eb = ((1.0f - tau) * c0.z + tau * c1.z) * vs;
+                q.er = e.x * vs;
+                q.eg = e.y * vs;
+                q.eb = e.z * vs;
                 q.pad = 0.0f;
                 s_rec[idx] = q;
                 const int br0 = q.jlo >> 2, br1 = q.jhi >> 2;
@@ -304,7 +315,8 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
 //   1. each lane takes 4 records: pixel box inside the square, and the rectangle of
 //      blocks it covers; live records are counted per rectangle;
 //   2. the live records are grouped by rectangle (warp-local counting sort), and their
-//      colour (colormap) and Gaussian scale are computed, one record per lane;
+//      colour (colormap, or the particle's emission in vector-colour scenes) and Gaussian
+//      scale are computed, one record per lane;
 //   3. for every rectangle present, one jump to straight-line code for that rectangle,
 //      which runs over its records: each lane evaluates its pixel of every covered block
 //      with the FP32 coverage rule and adds e * w to its registers.
@@ -422,7 +434,7 @@ __device__ __forceinline__ void run_dispatch(int id, const WarpSmem *ws, int j0,
 
 // kViewScale: multiply every record's emission by a per-view, per-species scale (plans
 // with a brightness sequence); a separate instance, so plain renders carry no extra code.
-template <int NR, int NC, bool kViewScale>
+template <int NR, int NC, bool kViewScale, bool kEmit>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCtas))
     k_splat_warp(SceneDev sc, FrameDev fr, int *queue, float *out, int out_accum, int split) {
     if (fr.status[kStatOverflow]) return;
@@ -554,22 +566,31 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 const float4 rec = recs[k];
                 const float R = rec.z;
                 const uint32_t code = __float_as_uint(rec.w);
-                const int type = (int)(code >> 24);
-                const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
-                const int len = __ldg(&sc.lut_len[type]);
-                const float f = It * (float)(len - 1);
-                const int kk = min((int)f, len - 2);
-                const float tau = f - (float)kk;
-                const int lo = __ldg(&sc.lut_off[type]) + kk;
-                const float4 c0 = __ldg(&sc.lut[lo]);
-                const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                int type;
+                float3 e;
+                if constexpr (kEmit) {
+                    const float4 em = __ldg(&sc.emit[code]);  // the code is the particle index
+                    type = __float_as_int(em.w);
+                    e = make_float3(em.x, em.y, em.z);
+                } else {
+                    type = (int)(code >> 24);
+                    const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
+                    const int len = __ldg(&sc.lut_len[type]);
+                    const float f = It * (float)(len - 1);
+                    const int kk = min((int)f, len - 2);
+                    const float tau = f - (float)kk;
+                    const int lo = __ldg(&sc.lut_off[type]) + kk;
+                    const float4 c0 = __ldg(&sc.lut[lo]);
+                    const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                    e = make_float3((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
+                                    (1.0f - tau) * c0.z + tau * c1.z);
+                }
                 const float R2 = __fmul_rn(R, R);
                 float vs = 1.0f;
                 if constexpr (kViewScale) vs = __ldg(&fr.vscale[v * sc.n_types + type]);
                 float4 *d = reinterpret_cast<float4 *>(&ws->dec[j]);  // in grouped order
                 d[0] = make_float4(rec.x, rec.y, R2, __fdividef(kexp, R2));
-                d[1] = make_float4(((1.0f - tau) * c0.x + tau * c1.x) * vs, ((1.0f - tau) * c0.y + tau * c1.y) * vs,
-                                   ((1.0f - tau) * c0.z + tau * c1.z) * vs, 0.0f);
+                d[1] = make_float4(e.x * vs, e.y * vs, e.z * vs, 0.0f);
             }
             __syncwarp();
             // ---- 3. one jump per rectangle present, then its records
@@ -648,9 +669,13 @@ constexpr int kWarpTileMax = 32;
 static bool warp_kernel(int T) { return T <= kWarpTileMax; }
 int splat_split(int T) { return T > 16 && warp_kernel(T) ? 2 : 1; }
 
-static WarpSplatFn warp_fn(int T, bool scaled = false) {
-    if (scaled) return T <= 8 ? k_splat_warp<2, 1, true> : k_splat_warp<4, 2, true>;
-    return T <= 8 ? k_splat_warp<2, 1, false> : k_splat_warp<4, 2, false>;
+static WarpSplatFn warp_fn(int T, bool scaled = false, bool emit = false) {
+    if (emit) {
+        if (scaled) return T <= 8 ? k_splat_warp<2, 1, true, true> : k_splat_warp<4, 2, true, true>;
+        return T <= 8 ? k_splat_warp<2, 1, false, true> : k_splat_warp<4, 2, false, true>;
+    }
+    if (scaled) return T <= 8 ? k_splat_warp<2, 1, true, false> : k_splat_warp<4, 2, true, false>;
+    return T <= 8 ? k_splat_warp<2, 1, false, false> : k_splat_warp<4, 2, false, false>;
 }
 
 static SplatFn cta_fn(int T) {
@@ -681,13 +706,13 @@ int splat_workers_per_sm(int T) { return splat_blocks_per_sm(T) * (warp_kernel(T
 cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, float *out, int out_accum,
                          int grid, cudaStream_t st) {
     const size_t smem = splat_smem(fr.T);
-    const bool scaled = fr.vscale != nullptr;
+    const bool scaled = fr.vscale != nullptr, emit = sc.emit != nullptr;
     cudaError_t err = ensure_smem_limit(
-        warp_kernel(fr.T) ? (const void *)warp_fn(fr.T, scaled) : splat_kernel(fr.T), smem);
+        warp_kernel(fr.T) ? (const void *)warp_fn(fr.T, scaled, emit) : splat_kernel(fr.T), smem);
     if (err != cudaSuccess) return err;
     if (warp_kernel(fr.T))
-        warp_fn(fr.T, scaled)<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum,
-                                                                             splat_split(fr.T));
+        warp_fn(fr.T, scaled, emit)<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum,
+                                                                                   splat_split(fr.T));
     else
         cta_fn(fr.T)<<<grid, splat_cta_threads(fr.T), smem, st>>>(sc, fr, queue, out, out_accum);
     return cudaGetLastError();

@@ -186,7 +186,8 @@ struct splotch_scene {
     Mem mem;
     void *attr = nullptr;
     void *meta = nullptr;
-    size_t attr_bytes = 0, meta_bytes = 0;
+    void *emit = nullptr;  // per-particle emission (vector-colour scenes)
+    size_t attr_bytes = 0, meta_bytes = 0, emit_bytes = 0;
     SceneDev dev_view{};
 };
 
@@ -232,6 +233,10 @@ static splotch_status validate_desc(const splotch_scene_desc *d) {
     }
     if ((d->allocator.alloc == nullptr) != (d->allocator.free == nullptr))
         return fail(SPLOTCH_ERR_INVALID_ARG, "give both allocator callbacks or neither");
+    if (d->col_vector && d->n > 0 && !d->rgb) {
+        for (int t = 0; t < d->n_types; ++t)
+            if (d->col_vector[t]) return fail(SPLOTCH_ERR_INVALID_ARG, "vector-coloured species %d without rgb", t);
+    }
     return SPLOTCH_OK;
 }
 
@@ -249,6 +254,85 @@ static splotch_status create_scene_impl(const splotch_scene_desc *d, splotch_sce
 
 extern "C" splotch_status splotch_create_scene(const splotch_scene_desc *d, splotch_scene **out) {
     return create_scene_impl(d, out, false);
+}
+
+// Per-particle emission of a scene with vector-coloured species (the scene's attributes
+// and colormaps are already on the device): ranges of the vector species' colour
+// components (given, or their joint min / max), then k_emission.  Sets sc->emit.
+static splotch_status build_emission(const splotch_scene_desc *d, splotch_scene *sc, bool copy_engine) {
+    cudaStream_t st = (cudaStream_t)d->stream;
+    sc->emit_bytes = align256(sizeof(float4) * (size_t)std::max<int64_t>(1, d->n));
+    sc->emit = sc->mem.alloc(sc->emit_bytes, st);
+    if (!sc->emit) return fail(SPLOTCH_ERR_OOM, "per-particle emission (%zu bytes)", sc->emit_bytes);
+    if (d->n == 0) return SPLOTCH_OK;
+    const int nt = d->n_types;
+    const size_t fb = sizeof(float) * 3 * (size_t)d->n;
+    // the colour field on the device: as given, through its device-visible address when
+    // page-locked, else staged
+    const float *rgb = d->on_device ? d->rgb : nullptr;
+    if (!rgb && !copy_engine) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, d->rgb) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            rgb = (const float *)pa.devicePointer;
+        else
+            cudaGetLastError();
+    }
+    Carve sv;
+    const size_t o_rgb = rgb ? 0 : sv.take(fb);
+    const size_t o_vec = sv.take(sizeof(int) * nt), o_lo = sv.take(sizeof(float) * nt);
+    const size_t o_hi = sv.take(sizeof(float) * nt), o_lg = sv.take(sizeof(int) * nt);
+    const size_t o_beta = sv.take(sizeof(float) * nt), o_keys = sv.take(sizeof(unsigned) * 2 * nt);
+    const size_t o_bad = sv.take(sizeof(int));
+    char *stg = (char *)sc->mem.alloc(sv.off, st);
+    if (!stg) return fail(SPLOTCH_ERR_OOM, "emission staging");
+    if (!rgb) {
+        cudaMemcpyAsync(stg + o_rgb, d->rgb, fb, cudaMemcpyHostToDevice, st);
+        rgb = (const float *)(stg + o_rgb);
+    }
+    std::vector<int> vec(nt), lg(d->i_log, d->i_log + nt);
+    std::vector<float> lo(nt, 0.0f), hi(nt, 0.0f);
+    for (int t = 0; t < nt; ++t) vec[t] = d->col_vector[t] != 0;
+    if (d->i_min) {
+        for (int t = 0; t < nt; ++t) lo[t] = d->i_min[t], hi[t] = d->i_max[t];
+    } else {
+        std::vector<unsigned> keys(2 * nt);
+        for (int t = 0; t < nt; ++t) keys[2 * t] = 0xFFFFFFFFu, keys[2 * t + 1] = 0u;
+        cudaMemcpyAsync(stg + o_keys, keys.data(), sizeof(unsigned) * keys.size(), cudaMemcpyHostToDevice, st);
+        for (int t = 0; t < nt; ++t) {
+            if (!vec[t]) continue;
+            cudaError_t e = launch_minmax(0, rgb, 3 * d->type_begin[t], 3 * d->type_begin[t + 1], d->i_log[t],
+                                          (unsigned *)(stg + o_keys) + 2 * t, st);
+            if (e != cudaSuccess) {
+                sc->mem.release(stg, st);
+                return fail(SPLOTCH_ERR_CUDA, "colour range: %s", cudaGetErrorString(e));
+            }
+        }
+        cudaMemcpyAsync(keys.data(), stg + o_keys, sizeof(unsigned) * keys.size(), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        for (int t = 0; t < nt; ++t) {
+            lo[t] = keys[2 * t] == 0xFFFFFFFFu ? 0.0f : order_key_inv(keys[2 * t]);
+            hi[t] = keys[2 * t + 1] == 0u ? 0.0f : order_key_inv(keys[2 * t + 1]);
+        }
+    }
+    cudaMemcpyAsync(stg + o_vec, vec.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(stg + o_lo, lo.data(), sizeof(float) * nt, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(stg + o_hi, hi.data(), sizeof(float) * nt, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(stg + o_lg, lg.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(stg + o_beta, d->brightness, sizeof(float) * nt, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(stg + o_bad, 0, sizeof(int), st);
+    cudaError_t e = launch_emission(sc->storage, sc->dev_view, rgb, (const int *)(stg + o_vec),
+                                    (const float *)(stg + o_lo), (const float *)(stg + o_hi),
+                                    (const int *)(stg + o_lg), (const float *)(stg + o_beta), (float4 *)sc->emit,
+                                    (int *)(stg + o_bad), st);
+    int bad = 0;
+    cudaMemcpyAsync(&bad, stg + o_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    sc->mem.release(stg, st);
+    if (e != cudaSuccess || se != cudaSuccess)
+        return fail(SPLOTCH_ERR_CUDA, "emission: %s", cudaGetErrorString(e != cudaSuccess ? e : se));
+    if (bad) return fail(SPLOTCH_ERR_INVALID_ARG, "non-finite colour component");
+    sc->dev_view.emit = (const float4 *)sc->emit;
+    return SPLOTCH_OK;
 }
 
 static splotch_status create_scene_impl(const splotch_scene_desc *d, splotch_scene **out, bool copy_engine) {
@@ -272,6 +356,7 @@ static splotch_status create_scene_impl(const splotch_scene_desc *d, splotch_sce
     auto cleanup = [&](splotch_status st_) {
         if (sc->attr) sc->mem.release(sc->attr, st);
         if (sc->meta) sc->mem.release(sc->meta, st);
+        if (sc->emit) sc->mem.release(sc->emit, st);
         cudaStreamSynchronize(st);
         delete sc;
         return st_;
@@ -412,6 +497,7 @@ static splotch_status create_scene_impl(const splotch_scene_desc *d, splotch_sce
     if (se != cudaSuccess) return cleanup(fail(SPLOTCH_ERR_CUDA, "create: %s", cudaGetErrorString(se)));
 
     SceneDev &v = sc->dev_view;
+    v.emit = nullptr;
     v.x = ab;
     v.y = ab + arr;
     v.z = ab + 2 * arr;
@@ -423,6 +509,12 @@ static splotch_status create_scene_impl(const splotch_scene_desc *d, splotch_sce
     v.lut = (const float4 *)(mb + o_lut);
     v.lut_off = (const int *)(mb + o_off);
     v.lut_len = (const int *)(mb + o_len);
+    bool any_vec = false;
+    for (int t = 0; d->col_vector && t < d->n_types; ++t) any_vec |= d->col_vector[t] != 0;
+    if (any_vec) {
+        s = build_emission(d, sc, copy_engine);
+        if (s != SPLOTCH_OK) return cleanup(s);
+    }
     *out = sc;
     return SPLOTCH_OK;
 }
@@ -431,6 +523,7 @@ extern "C" splotch_status splotch_destroy(splotch_scene *sc) {
     if (!sc) return SPLOTCH_OK;
     sc->mem.release(sc->attr, 0);
     sc->mem.release(sc->meta, 0);
+    sc->mem.release(sc->emit, 0);
     cudaStreamSynchronize(0);
     delete sc;
     return SPLOTCH_OK;
@@ -442,7 +535,7 @@ extern "C" splotch_status splotch_scene_info(const splotch_scene *sc, int64_t *n
     if (n) *n = sc->n;
     if (n_types) *n_types = sc->n_types;
     if (storage) *storage = sc->storage;
-    if (device_bytes) *device_bytes = (int64_t)(sc->attr_bytes + sc->meta_bytes);
+    if (device_bytes) *device_bytes = (int64_t)(sc->attr_bytes + sc->meta_bytes + sc->emit_bytes);
     return SPLOTCH_OK;
 }
 
@@ -1212,6 +1305,46 @@ extern "C" splotch_status splotch_render_noalloc(splotch_scene *sc, const splotc
 // page-locked host memory, or staged), so the host-to-device transfer overlaps the render.
 
 // Exact per-species range of the (logged) intensity over the whole set, chunk by chunk.
+// Joint min / max keys of `comps`-component field values over the species with use[t],
+// read chunk by chunk (through a device-visible address when the field is device or
+// page-locked memory, else staged).
+static cudaError_t field_ranges(const splotch_scene_desc *d, const float *field, int comps, const std::vector<int> &use,
+                                int64_t chunk, cudaStream_t st, Mem &mem, unsigned *keys) {
+    cudaPointerAttributes pa{};
+    bool direct = d->on_device != 0;
+    const float *dev_in = field;
+    if (!direct && cudaPointerGetAttributes(&pa, field) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer) {
+        direct = true;
+        dev_in = (const float *)pa.devicePointer;
+    }
+    cudaGetLastError();
+    float *stage = nullptr;
+    if (!direct) {
+        stage = (float *)mem.alloc(sizeof(float) * comps * (size_t)std::min<int64_t>(chunk, d->n), st);
+        if (!stage) return cudaErrorMemoryAllocation;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int64_t b = 0; b < d->n && e == cudaSuccess; b += chunk) {
+        const int64_t len = std::min(chunk, d->n - b);
+        const float *src = dev_in + comps * b;
+        if (!direct) {
+            e = cudaMemcpyAsync(stage, field + comps * b, sizeof(float) * comps * len, cudaMemcpyHostToDevice, st);
+            src = stage;
+        }
+        for (int t = 0; t < d->n_types && e == cudaSuccess; ++t) {
+            const int64_t a0 = std::max(b, d->type_begin[t]), a1 = std::min(b + len, d->type_begin[t + 1]);
+            if (use[t] && a1 > a0)
+                e = launch_minmax(0, src - comps * b, comps * a0, comps * a1, d->i_log[t], keys + 2 * t, st);
+        }
+        if (!direct && e == cudaSuccess) e = cudaStreamSynchronize(st);  // staging reused
+    }
+    if (stage) mem.release(stage, st);
+    return e;
+}
+
+// Per-species ranges over the whole set (given, or the joint min / max of the intensity,
+// or of the colour components for vector-coloured species), so every chunk normalises alike.
 static splotch_status streamed_ranges(const splotch_scene_desc *d, int64_t chunk, cudaStream_t st, Mem &mem,
                                       std::vector<float> &lo, std::vector<float> &hi) {
     lo.assign(d->n_types, 0.0f);
@@ -1220,39 +1353,21 @@ static splotch_status streamed_ranges(const splotch_scene_desc *d, int64_t chunk
         for (int t = 0; t < d->n_types; ++t) lo[t] = d->i_min[t], hi[t] = d->i_max[t];
         return SPLOTCH_OK;
     }
-    const size_t kb = align256(sizeof(unsigned) * 2 * d->n_types);
-    cudaPointerAttributes pa{};
-    bool direct = d->on_device != 0;
-    const float *dev_in = d->intensity;
-    if (!direct && cudaPointerGetAttributes(&pa, d->intensity) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-        pa.devicePointer) {
-        direct = true;
-        dev_in = (const float *)pa.devicePointer;
-    }
-    cudaGetLastError();
-    const size_t stage = direct ? 0 : sizeof(float) * (size_t)std::min<int64_t>(chunk, d->n);
-    char *buf = (char *)mem.alloc(kb + stage, st);
-    if (!buf) return fail(SPLOTCH_ERR_OOM, "range staging");
-    unsigned *keys = (unsigned *)buf;
+    unsigned *keys = (unsigned *)mem.alloc(align256(sizeof(unsigned) * 2 * d->n_types), st);
+    if (!keys) return fail(SPLOTCH_ERR_OOM, "range staging");
     std::vector<unsigned> init(2 * d->n_types);
     for (int t = 0; t < d->n_types; ++t) init[2 * t] = 0xFFFFFFFFu, init[2 * t + 1] = 0u;
+    std::vector<int> scalar(d->n_types, 1), vector(d->n_types, 0);
+    bool any_vec = false;
+    for (int t = 0; d->col_vector && t < d->n_types; ++t)
+        if (d->col_vector[t]) scalar[t] = 0, vector[t] = 1, any_vec = true;
     cudaError_t e = cudaMemcpyAsync(keys, init.data(), sizeof(unsigned) * init.size(), cudaMemcpyHostToDevice, st);
-    for (int64_t b = 0; b < d->n && e == cudaSuccess; b += chunk) {
-        const int64_t len = std::min(chunk, d->n - b);
-        const float *src = dev_in + b;
-        if (!direct) {
-            e = cudaMemcpyAsync(buf + kb, d->intensity + b, sizeof(float) * len, cudaMemcpyHostToDevice, st);
-            src = (const float *)(buf + kb);
-        }
-        for (int t = 0; t < d->n_types && e == cudaSuccess; ++t) {
-            const int64_t a0 = std::max(b, d->type_begin[t]), a1 = std::min(b + len, d->type_begin[t + 1]);
-            if (a1 > a0) e = launch_minmax(0, src - b, a0, a1, d->i_log[t], keys + 2 * t, st);
-        }
-        if (!direct && e == cudaSuccess) e = cudaStreamSynchronize(st);  // staging reused
-    }
+    if (e == cudaSuccess) e = field_ranges(d, d->intensity, 1, scalar, chunk, st, mem, keys);
+    if (e == cudaSuccess && any_vec) e = field_ranges(d, d->rgb, 3, vector, chunk, st, mem, keys);
     if (e == cudaSuccess) e = cudaMemcpyAsync(init.data(), keys, sizeof(unsigned) * init.size(), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    mem.release(buf, st);
+    mem.release(keys, st);
+    if (e == cudaErrorMemoryAllocation) return fail(SPLOTCH_ERR_OOM, "range staging");
     if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "intensity range: %s", cudaGetErrorString(e));
     for (int t = 0; t < d->n_types; ++t) {
         lo[t] = init[2 * t] == 0xFFFFFFFFu ? 0.0f : order_key_inv(init[2 * t]);
@@ -1308,6 +1423,7 @@ extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, i
         cd.n = len;
         const float *const *p = src;
         cd.x = p[0] + b, cd.y = p[1] + b, cd.z = p[2] + b, cd.h = p[3] + b, cd.intensity = p[4] + b;
+        cd.rgb = d->rgb ? d->rgb + 3 * b : nullptr;
         std::vector<int64_t> tb(d->n_types + 1);
         for (int t = 0; t <= d->n_types; ++t) tb[t] = std::min(std::max(d->type_begin[t] - b, (int64_t)0), len);
         cd.type_begin = tb.data();

@@ -54,6 +54,9 @@ struct SceneDev {
     const float4 *lut;               // brightness x colormap entries, all species
     const int *lut_off;              // [n_types]
     const int *lut_len;              // [n_types]
+    const float4 *emit;              // [n] {r, g, b, species bits}: per-particle emission
+                                     // (vector colour scenes; records then carry particle
+                                     // indices), or null
 };
 
 // Per-frame buffers (one frame = V views).
@@ -270,6 +273,9 @@ __device__ __forceinline__ float ex2_fast(float x) {
 
 cudaError_t launch_minmax(int storage_in_f32_only, const float *I, int64_t begin, int64_t end, int i_log,
                           unsigned *keys, cudaStream_t st);
+cudaError_t launch_emission(int storage, const SceneDev &sc, const float *rgb, const int *vec, const float *lo,
+                            const float *hi, const int *lg, const float *beta, float4 *emit, int *bad,
+                            cudaStream_t st);
 cudaError_t launch_prepare(const float *x, const float *y, const float *z, const float *h,
                            const float *I, int64_t n, int n_types, const int64_t *type_begin,
                            const float *lo, const float *hi, const int *i_log, int storage,

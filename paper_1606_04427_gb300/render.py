@@ -129,6 +129,16 @@ def _scene_desc(ps, storage: str, stream=None, allocator=None):
     if ps.i_min is not None and ps.i_max is not None:
         d.i_min = arr(ps.i_min, np.float32)
         d.i_max = arr(ps.i_max, np.float32)
+    vec = getattr(ps, "col_vector", None)
+    if vec is not None and np.any(np.asarray(vec)):
+        d.col_vector = arr(vec, np.int32)
+        if n > 0:
+            if on_dev:
+                c = torch.as_tensor(ps.rgb, device="cuda").contiguous().float().reshape(n, 3)
+                keep.append(c)
+                d.rgb = c.data_ptr()
+            else:
+                d.rgb = arr(np.asarray(ps.rgb).reshape(n, 3), np.float32)
     if allocator is not None:
         d.allocator = allocator.c()
         keep.append(allocator)
@@ -267,6 +277,13 @@ class Scene:
         for t in range(nt):
             mem[offs_h[t]:offs_h[t + 1]].sort()
         return counts_h, offs_h, mem
+
+    def info(self):
+        """(particle count, species count, storage code, device bytes held)."""
+        n, t, st, b = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int64()
+        check(self._lib.splotch_scene_info(self.handle, C.byref(n), C.byref(t), C.byref(st), C.byref(b)),
+              "scene_info")
+        return n.value, t.value, st.value, b.value
 
     def workspace_bytes(self, width: int, height: int, tile: int, pairs: int) -> int:
         return int(self._lib.splotch_workspace_bytes(self.handle, int(width), int(height), int(tile),

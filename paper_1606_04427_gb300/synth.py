@@ -246,6 +246,28 @@ def two_species_set(n_gas: int, n_star: int, seed: int, grid: int = 256) -> Part
                        name="two_species")
 
 
+def with_vector_colour(ps: ParticleSet, species: Sequence[int], seed: int = 0) -> ParticleSet:
+    """The same set with the given species coloured from a vector field (Section 2.1):
+    a per-particle RGB triple, here a smooth positive field of position with lognormal
+    scatter (like velocity or chemical-abundance components mapped to colour), drawn for
+    every particle; the other species keep their colormap."""
+    rng = np.random.default_rng(seed)
+    n = ps.n
+    k = rng.uniform(2.0, 6.0, size=(3, 3))
+    ph = rng.uniform(0.0, 2.0 * np.pi, size=3)
+    pos = np.stack([ps.x, ps.y, ps.z], axis=1).astype(np.float32)
+    rgb = np.empty((n, 3), np.float32)
+    for c in range(3):
+        rgb[:, c] = 1.2 + np.sin(pos @ k[c].astype(np.float32) * np.float32(2.0 * np.pi) + np.float32(ph[c]))
+    rgb *= np.exp(rng.normal(0.0, 0.25, size=(n, 3))).astype(np.float32)
+    out = ParticleSet(**{f: getattr(ps, f) for f in ps.__dataclass_fields__})
+    out.rgb = rgb
+    vec = np.zeros(ps.n_types, np.int32)
+    vec[list(species)] = 1
+    out.col_vector = vec
+    return out
+
+
 def front_camera(width: int, height: int, distance: float = 2.0, fov_deg: float = 45.0) -> Camera:
     """Camera on the +z axis at ``distance`` from the box centre, looking at it."""
     c = CENTRE
