@@ -273,6 +273,20 @@ splotch_status splotch_plan_set_cameras(splotch_plan *plan, const splotch_camera
  * Errors: INVALID_ARG (NULL plan, a negative or non-finite scale), CUDA. */
 splotch_status splotch_plan_set_brightness(splotch_plan *plan, const float *scale, void *stream);
 
+/* Per-view colormaps of a plan (Section 2.1: a scene file varies parameters such as the
+ * colour palette over a progression of images).  cmap_rgb: host, n_views x n_types
+ * pointers (view-major), each to cmap_len[v * n_types + t] RGB triples (FP32, finite,
+ * 2..2^20 entries): the colormap of species t in view v, times the scene's brightness of
+ * t (a brightness sequence still applies on top); NULL resets every view to the scene's
+ * colormaps.  Palette thresholds are colormaps whose entries below / above a threshold
+ * repeat the end colours.  The next launch (or graph replay) renders with these
+ * colormaps; a captured graph is captured again when the plan's colormap storage moves.
+ * Stream-ordered on `stream`, which it synchronises.  Errors: INVALID_ARG (NULL plan, a
+ * bad colormap), UNSUPPORTED (a scene with vector colour, whose emission is per
+ * particle), OOM, CUDA. */
+splotch_status splotch_plan_set_colormaps(splotch_plan *plan, const float *const *cmap_rgb,
+                                          const int32_t *cmap_len, void *stream);
+
 /* Enqueue one batch render into out (device, n_views x H x W x 3 FP32). */
 splotch_status splotch_plan_launch(splotch_plan *plan, float *out, void *stream);
 

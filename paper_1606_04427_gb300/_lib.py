@@ -84,6 +84,7 @@ SIGNATURES = {
                                 C.c_void_p], C.c_int),
     "splotch_debug_sort": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p], C.c_int),
     "splotch_plan_set_brightness": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "splotch_plan_set_colormaps": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "splotch_render_streamed": ([C.POINTER(SceneDesc), C.c_int64, C.POINTER(CameraC), C.POINTER(RenderParamsC),
                                  C.c_void_p, C.c_void_p], C.c_int),
     "splotch_render_noalloc": ([C.c_void_p, C.POINTER(CameraC), C.POINTER(RenderParamsC), C.c_void_p,

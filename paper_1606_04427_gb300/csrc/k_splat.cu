@@ -181,13 +181,16 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 } else {
                     type = (int)(code >> 24);
                     const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
-                    const int len = __ldg(&sc.lut_len[type]);
+                    const bool per_view = fr.vlut != nullptr;  // the view's colormap in a plan
+                    const int vi = v * sc.n_types + type;
+                    const float4 *lut = per_view ? fr.vlut : sc.lut;
+                    const int len = per_view ? __ldg(&fr.vlut_len[vi]) : __ldg(&sc.lut_len[type]);
+                    const int off = per_view ? __ldg(&fr.vlut_off[vi]) : __ldg(&sc.lut_off[type]);
                     const float f = It * (float)(len - 1);
                     const int kk = min((int)f, len - 2);
                     const float tau = f - (float)kk;
-                    const int lo = __ldg(&sc.lut_off[type]) + kk;
-                    const float4 c0 = __ldg(&sc.lut[lo]);
-                    const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                    const float4 c0 = __ldg(&lut[off + kk]);
+                    const float4 c1 = __ldg(&lut[off + kk + 1]);
                     e = make_float3((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
                                     (1.0f - tau) * c0.z + tau * c1.z);
                 }
@@ -575,13 +578,23 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 } else {
                     type = (int)(code >> 24);
                     const float It = fminf((float)(code & kCodeMax) * (1.0f / (float)kCodeMax), 1.0f);
-                    const int len = __ldg(&sc.lut_len[type]);
+                    // the view's colormap in a plan with per-view sequences, else the scene's
+                    const float4 *lut = sc.lut;
+                    int len, off;
+                    if constexpr (kViewScale) {
+                        const int vi = v * sc.n_types + type;
+                        lut = fr.vlut;
+                        len = __ldg(&fr.vlut_len[vi]);
+                        off = __ldg(&fr.vlut_off[vi]);
+                    } else {
+                        len = __ldg(&sc.lut_len[type]);
+                        off = __ldg(&sc.lut_off[type]);
+                    }
                     const float f = It * (float)(len - 1);
                     const int kk = min((int)f, len - 2);
                     const float tau = f - (float)kk;
-                    const int lo = __ldg(&sc.lut_off[type]) + kk;
-                    const float4 c0 = __ldg(&sc.lut[lo]);
-                    const float4 c1 = __ldg(&sc.lut[lo + 1]);
+                    const float4 c0 = __ldg(&lut[off + kk]);
+                    const float4 c1 = __ldg(&lut[off + kk + 1]);
                     e = make_float3((1.0f - tau) * c0.x + tau * c1.x, (1.0f - tau) * c0.y + tau * c1.y,
                                     (1.0f - tau) * c0.z + tau * c1.z);
                 }

@@ -183,6 +183,7 @@ struct splotch_scene {
     int n_types = 0;
     int storage = 0;
     std::vector<int64_t> type_begin;
+    std::vector<float> brightness;  // per species
     Mem mem;
     void *attr = nullptr;
     void *meta = nullptr;
@@ -350,6 +351,7 @@ static splotch_status create_scene_impl(const splotch_scene_desc *d, splotch_sce
     sc->n_types = d->n_types;
     sc->storage = d->storage;
     sc->type_begin.assign(d->type_begin, d->type_begin + d->n_types + 1);
+    sc->brightness.assign(d->brightness, d->brightness + d->n_types);
     sc->mem.a = d->allocator;
     sc->mem.dev = dev;
 
@@ -986,6 +988,12 @@ struct splotch_plan {
     cudaGraphExec_t exec = nullptr;
     float *exec_out = nullptr;
     float *vscale = nullptr;  // device [V * n_types] emission scale per view and species
+    // per-view colormaps: device [2 * V * n_types] (offsets, then lengths) into vlut, which
+    // is the scene's LUT until splotch_plan_set_colormaps loads the plan's own (lut_buf)
+    int *vlut_tab = nullptr;
+    const float4 *vlut = nullptr;
+    float4 *lut_buf = nullptr;
+    size_t lut_cap = 0;  // entries
 };
 
 static splotch_status plan_enqueue(splotch_plan *pl, float *out, cudaStream_t st) {
@@ -993,6 +1001,10 @@ static splotch_status plan_enqueue(splotch_plan *pl, float *out, cudaStream_t st
     FrameHost &fh = pl->fh;
     FrameDev fr = frame_dev(fh, pl->fixed, pl->var);
     fr.vscale = pl->vscale;
+    const size_t nvt = (size_t)fh.V * sc->n_types;
+    fr.vlut = pl->vlut;
+    fr.vlut_off = pl->vlut_tab;
+    fr.vlut_len = pl->vlut_tab + nvt;
     CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_counts, 0, sizeof(int) * (size_t)fh.V * fh.n_tiles, st));
     CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_status, 0, sizeof(int) * 4, st));
     CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_queue, 0, sizeof(int) * 4, st));
@@ -1014,6 +1026,8 @@ extern "C" splotch_status splotch_plan_destroy(splotch_plan *pl) {
     if (pl->var) pl->sc->mem.release(pl->var, 0);
     if (pl->fixed) pl->sc->mem.release(pl->fixed, 0);
     if (pl->vscale) pl->sc->mem.release(pl->vscale, 0);
+    if (pl->vlut_tab) pl->sc->mem.release(pl->vlut_tab, 0);
+    if (pl->lut_buf) pl->sc->mem.release(pl->lut_buf, 0);
     if (pl->box) cudaFreeHost(pl->box);
     cudaStreamSynchronize(0);
     delete pl;
@@ -1079,6 +1093,20 @@ extern "C" splotch_status splotch_plan_create(splotch_scene *sc, const splotch_c
             splotch_plan_destroy(pl);
             return fail(SPLOTCH_ERR_OOM, "plan view scales");
         }
+        // every view starts with the scene's colormaps
+        std::vector<int> tab(2 * nv);
+        std::vector<int> off(sc->n_types), len(sc->n_types);
+        cudaMemcpy(off.data(), sc->dev_view.lut_off, sizeof(int) * sc->n_types, cudaMemcpyDeviceToHost);
+        cudaMemcpy(len.data(), sc->dev_view.lut_len, sizeof(int) * sc->n_types, cudaMemcpyDeviceToHost);
+        for (size_t k = 0; k < nv; ++k) tab[k] = off[k % sc->n_types], tab[nv + k] = len[k % sc->n_types];
+        pl->vlut_tab = (int *)sc->mem.alloc(sizeof(int) * 2 * nv, st);
+        pl->vlut = sc->dev_view.lut;
+        if (!pl->vlut_tab ||
+            cudaMemcpyAsync(pl->vlut_tab, tab.data(), sizeof(int) * 2 * nv, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            splotch_plan_destroy(pl);
+            return fail(SPLOTCH_ERR_OOM, "plan colormap table");
+        }
     }
     *out = pl;
     return SPLOTCH_OK;
@@ -1115,6 +1143,71 @@ extern "C" splotch_status splotch_plan_set_brightness(splotch_plan *pl, const fl
         }
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(cudaMemcpyAsync(pl->vscale, v.data(), sizeof(float) * nv, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_plan_set_colormaps(splotch_plan *pl, const float *const *cmap_rgb,
+                                                     const int32_t *cmap_len, void *stream) {
+    if (!pl) return fail(SPLOTCH_ERR_INVALID_ARG, "plan is NULL");
+    splotch_scene *sc = pl->sc;
+    if (sc->dev_view.emit)
+        return fail(SPLOTCH_ERR_UNSUPPORTED, "per-view colormaps of a scene with vector colour (its colour is per particle)");
+    const int nt = sc->n_types;
+    const size_t nv = (size_t)pl->rs.V * nt;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> tab(2 * nv);
+    if (!cmap_rgb) {
+        // back to the scene's colormaps
+        std::vector<int> off(nt), len(nt);
+        CUDA_TRY(cudaMemcpy(off.data(), sc->dev_view.lut_off, sizeof(int) * nt, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(len.data(), sc->dev_view.lut_len, sizeof(int) * nt, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < nv; ++k) tab[k] = off[k % nt], tab[nv + k] = len[k % nt];
+        if (pl->vlut != sc->dev_view.lut && pl->exec) {
+            cudaGraphExecDestroy(pl->exec);  // captured with the plan's LUT: capture again
+            pl->exec = nullptr;
+        }
+        pl->vlut = sc->dev_view.lut;
+    } else {
+        if (!cmap_len) return fail(SPLOTCH_ERR_INVALID_ARG, "cmap_len is NULL");
+        size_t total = 0;
+        for (size_t k = 0; k < nv; ++k) {
+            if (cmap_len[k] < 2 || cmap_len[k] > (1 << 20) || !cmap_rgb[k])
+                return fail(SPLOTCH_ERR_INVALID_ARG, "colormap of view %zu, species %zu: NULL or not 2..2^20 entries",
+                            k / nt, k % nt);
+            for (int j = 0; j < 3 * cmap_len[k]; ++j)
+                if (!std::isfinite(cmap_rgb[k][j]))
+                    return fail(SPLOTCH_ERR_INVALID_ARG, "colormap of view %zu, species %zu not finite", k / nt, k % nt);
+            tab[k] = (int)total;
+            tab[nv + k] = cmap_len[k];
+            total += (size_t)cmap_len[k];
+        }
+        if (total > (size_t)INT32_MAX) return fail(SPLOTCH_ERR_UNSUPPORTED, "colormaps above 2^31 entries");
+        // entries premultiplied by the species brightness, as the scene's
+        const std::vector<float> &bright = sc->brightness;
+        std::vector<float> lut(4 * total);
+        for (size_t k = 0; k < nv; ++k)
+            for (int j = 0; j < cmap_len[k]; ++j) {
+                float *q = &lut[4 * ((size_t)tab[k] + j)];
+                for (int c = 0; c < 3; ++c) q[c] = bright[k % nt] * cmap_rgb[k][3 * j + c];
+                q[3] = 0.0f;
+            }
+        if (total > pl->lut_cap) {
+            float4 *nb = (float4 *)sc->mem.alloc(sizeof(float4) * total, st);
+            if (!nb) return fail(SPLOTCH_ERR_OOM, "plan colormaps (%zu entries)", total);
+            CUDA_TRY(cudaStreamSynchronize(st));  // no launch of this plan may still read the old one
+            if (pl->lut_buf) sc->mem.release(pl->lut_buf, st);
+            pl->lut_buf = nb;
+            pl->lut_cap = total;
+        }
+        if (pl->vlut != pl->lut_buf && pl->exec) {
+            cudaGraphExecDestroy(pl->exec);  // the captured kernels read another LUT: capture again
+            pl->exec = nullptr;
+        }
+        pl->vlut = pl->lut_buf;
+        CUDA_TRY(cudaMemcpyAsync(pl->lut_buf, lut.data(), sizeof(float) * lut.size(), cudaMemcpyHostToDevice, st));
+    }
+    CUDA_TRY(cudaMemcpyAsync(pl->vlut_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     return SPLOTCH_OK;
 }

@@ -81,6 +81,10 @@ struct FrameDev {
     int64_t pair_cap;
     int item_cap, split_cap;
     const float *vscale;      // [V * n_types] emission scale per view and species, or null
+    // per-view colormaps (set with vscale): entries (premultiplied by brightness) of
+    // view v, species t at vlut[vlut_off[v * n_types + t] ...], vlut_len[...] of them
+    const float4 *vlut;
+    const int *vlut_off, *vlut_len;
 };
 
 enum { kSizePairs = 0, kSizeItems = 1, kSizeSplits = 2, kSizeK = 3, kSizeMaxCount = 4 };

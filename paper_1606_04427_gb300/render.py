@@ -345,6 +345,19 @@ class Plan:
             ptr = keep.ctypes.data
         check(self._lib.splotch_plan_set_brightness(self._h, ptr, _stream_handle(stream)), "plan_set_brightness")
 
+    def set_colormaps(self, cmaps=None, stream=None) -> None:
+        """Per-view colormaps: cmaps[v][t] an (entries x 3) array for species t in view v
+        (None resets every view to the scene's colormaps), from the next launch on."""
+        if cmaps is None:
+            check(self._lib.splotch_plan_set_colormaps(self._h, None, None, _stream_handle(stream)),
+                  "plan_set_colormaps")
+            return
+        flat = [np.ascontiguousarray(c, np.float32).reshape(-1, 3) for row in cmaps for c in row]
+        ptrs = (C.c_void_p * len(flat))(*[c.ctypes.data for c in flat])
+        lens = np.array([c.shape[0] for c in flat], np.int32)
+        check(self._lib.splotch_plan_set_colormaps(self._h, C.cast(ptrs, C.c_void_p), lens.ctypes.data,
+                                                   _stream_handle(stream)), "plan_set_colormaps")
+
     def new_output(self) -> torch.Tensor:
         return torch.empty((self.V, self.H, self.W, 3), dtype=torch.float32, device="cuda")
 

@@ -244,3 +244,72 @@ def test_plan_per_view_brightness_matches_rescaled_scenes():
     with pytest.raises(_lib.SplotchError):
         plan.set_brightness(np.full((3, 2), -1.0, np.float32))
     plan.close()
+
+
+def _thresholded(cmap, lo, hi):
+    """Palette thresholds as a colormap: below lo and above hi the end colours repeat
+    (resampled to 512 entries)."""
+    t = np.linspace(0.0, 1.0, 512)
+    u = np.clip((t - lo) / (hi - lo), 0.0, 1.0) * (cmap.shape[0] - 1)
+    k = np.minimum(u.astype(np.int64), cmap.shape[0] - 2)
+    f = (u - k)[:, None]
+    return ((1.0 - f) * cmap[k] + f * cmap[k + 1]).astype(np.float32)
+
+
+def test_plan_per_view_colormaps_match_the_oracle():
+    """A colormap sequence over the views of one plan (graph replays), alone and with a
+    brightness sequence, against the FP64 oracle rendering each view with that view's
+    colormaps; None restores the scene's; a vector-colour scene refuses it."""
+    import oracle
+    ps = synth.two_species_set(30000, 10000, 17, grid=32).with_brightness([0.05, 0.3])
+    cams = synth.orbit_cameras(3, 128, 96)
+    rng = np.random.default_rng(3)
+    maps = [[synth.smooth_ramp_cmap(rng, n=int(rng.integers(2, 300))) for _ in range(2)] for _ in range(3)]
+    maps[1][0] = _thresholded(ps.cmaps[0], 0.2, 0.6)  # palette thresholds on the gas
+    sc = render.Scene(ps, "f32")
+    plan = render.Plan(sc, cams, render.RenderParams(tile=16), graph=True)
+    out = plan.new_output()
+    plan.launch(out)
+    plain = out.clone()
+
+    def check(scale):
+        for v, cam in enumerate(cams):
+            pv = ps.with_brightness(ps.brightness * (1.0 if scale is None else scale[v]))
+            pv.cmaps = maps[v]
+            want = oracle.final(oracle.render(pv, cam))
+            assert np.abs(out[v].cpu().numpy() - want).max() <= 1e-4, v
+
+    plan.set_colormaps(maps)
+    plan.launch(out)
+    plan.launch(out)
+    plan.check()
+    check(None)
+    scale = np.array([[1.0, 0.5], [2.0, 1.0], [0.3, 3.0]], np.float32)
+    plan.set_brightness(scale)
+    plan.launch(out)
+    plan.check()
+    check(scale)
+    # larger maps move the plan's colormap storage: the graph is captured again
+    maps = [[synth.smooth_ramp_cmap(rng, n=4096) for _ in range(2)] for _ in range(3)]
+    plan.set_colormaps(maps)
+    plan.launch(out)
+    plan.check()
+    check(scale)
+    plan.set_brightness(None)
+    plan.set_colormaps(None)
+    plan.launch(out)
+    plan.check()
+    assert torch.abs(out - plain).max().item() <= 1e-6
+    with pytest.raises(_lib.SplotchError) as e:
+        plan.set_colormaps([[np.full((3, 3), np.nan, np.float32)] * 2] * 3)
+    assert e.value.status == _lib.INVALID_ARG
+    plan.close()
+    sc.close()
+    vec = synth.with_vector_colour(ps, [1], 1)
+    sv = render.Scene(vec, "f32")
+    pv = render.Plan(sv, cams, render.RenderParams(tile=16))
+    with pytest.raises(_lib.SplotchError) as e:
+        pv.set_colormaps(maps)
+    assert e.value.status == _lib.UNSUPPORTED
+    pv.close()
+    sv.close()
