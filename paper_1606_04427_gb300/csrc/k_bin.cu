@@ -738,9 +738,12 @@ cudaError_t launch_debug_raster(int storage, const SceneDev &sc, const ViewParam
 //   k_expand         each particle's records at its slots, keyed by tile id;
 //   (stable radix sort by tile id: each tile's records stay in depth order)
 
+// krange: {min, max} of the active particles' depth keys (atomicMin / atomicMax; the
+// caller sets {all ones, 0} first), so that the sort covers only the bits they span.
 template <int S>
 __global__ void __launch_bounds__(256) k_depth_records(SceneDev sc, const ViewParams *__restrict__ views,
-                                                       float4 *prec, uint32_t *dkey, uint32_t *pid) {
+                                                       float4 *prec, uint32_t *dkey, uint32_t *pid,
+                                                       uint32_t *krange) {
     __shared__ ViewParams s_v;
     __shared__ int64_t s_tb[kMaxTypes + 1];
     if (threadIdx.x == 0) s_v = views[0];
@@ -748,6 +751,7 @@ __global__ void __launch_bounds__(256) k_depth_records(SceneDev sc, const ViewPa
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int type = 0;
+    uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sc.n; i += stride) {
         while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
         Raster r;
@@ -755,8 +759,25 @@ __global__ void __launch_bounds__(256) k_depth_records(SceneDev sc, const ViewPa
                                     load1<S>(sc.h, i), r);
         prec[i] = make_float4(r.X, r.Y, r.R,
                               sc.emit ? __uint_as_float((uint32_t)i) : record_code(type, load1<S>(sc.it, i)));
-        dkey[i] = act ? (uint32_t)depth_key(r.zc) : kInactiveKey;
+        const uint32_t k = act ? depth_key(r.zc) : kInactiveKey;
+        dkey[i] = k;
         pid[i] = (uint32_t)i;
+        if (act) kmin = min(kmin, k), kmax = max(kmax, k);
+    }
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
+        atomicMin(&krange[0], kmin);
+        atomicMax(&krange[1], kmax);
+    }
+}
+
+// Depth keys relative to the smallest active one (active: key - base in [0, span];
+// inactive: span + 1, sorted last).
+__global__ void k_rebase_keys(uint32_t *dkey, int64_t n, uint32_t base, uint32_t span) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = dkey[i];
+        dkey[i] = k == kInactiveKey ? span + 1u : k - base;
     }
 }
 
@@ -772,8 +793,8 @@ __device__ __forceinline__ void tile_box(const ViewParams &v, float X, float Y, 
 __global__ void __launch_bounds__(256) k_sorted_counts(const ViewParams *__restrict__ views,
                                                        const float4 *__restrict__ prec,
                                                        const uint32_t *__restrict__ skey,
-                                                       const uint32_t *__restrict__ spid, int64_t n, float4 *srec,
-                                                       uint32_t *cnt) {
+                                                       const uint32_t *__restrict__ spid, int64_t n,
+                                                       uint32_t inactive, float4 *srec, uint32_t *cnt) {
     __shared__ ViewParams s_v;
     if (threadIdx.x == 0) s_v = views[0];
     __syncthreads();
@@ -784,7 +805,7 @@ __global__ void __launch_bounds__(256) k_sorted_counts(const ViewParams *__restr
         const int64_t q = base + lane;
         float4 rec = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-        if (q < n && skey[q] != kInactiveKey) {
+        if (q < n && skey[q] != inactive) {
             rec = prec[spid[q]];
             tile_box(s_v, rec.x, rec.y, rec.z, tx0, tx1, ty0, ty1);
         }
@@ -896,19 +917,26 @@ static int stream_grid(int64_t n, int threads) {
 }
 
 cudaError_t launch_depth_records(int storage, const SceneDev &sc, const ViewParams *views, float4 *prec,
-                                 uint32_t *dkey, uint32_t *pid, cudaStream_t st) {
+                                 uint32_t *dkey, uint32_t *pid, uint32_t *krange, cudaStream_t st) {
     if (sc.n <= 0) return cudaSuccess;
     const int g = stream_grid(sc.n, 256);
-    if (storage == 0) k_depth_records<0><<<g, 256, 0, st>>>(sc, views, prec, dkey, pid);
-    else if (storage == 1) k_depth_records<1><<<g, 256, 0, st>>>(sc, views, prec, dkey, pid);
-    else k_depth_records<2><<<g, 256, 0, st>>>(sc, views, prec, dkey, pid);
+    if (storage == 0) k_depth_records<0><<<g, 256, 0, st>>>(sc, views, prec, dkey, pid, krange);
+    else if (storage == 1) k_depth_records<1><<<g, 256, 0, st>>>(sc, views, prec, dkey, pid, krange);
+    else k_depth_records<2><<<g, 256, 0, st>>>(sc, views, prec, dkey, pid, krange);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebase_keys(uint32_t *dkey, int64_t n, uint32_t base, uint32_t span, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_rebase_keys<<<stream_grid(n, 256), 256, 0, st>>>(dkey, n, base, span);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sorted_counts(const ViewParams *views, const float4 *prec, const uint32_t *skey,
-                                 const uint32_t *spid, int64_t n, float4 *srec, uint32_t *cnt, cudaStream_t st) {
-    k_sorted_counts<<<stream_grid(std::max<int64_t>(1, n), 256), 256, 0, st>>>(views, prec, skey, spid, n, srec,
-                                                                               cnt);
+                                 const uint32_t *spid, int64_t n, uint32_t inactive, float4 *srec, uint32_t *cnt,
+                                 cudaStream_t st) {
+    k_sorted_counts<<<stream_grid(std::max<int64_t>(1, n), 256), 256, 0, st>>>(views, prec, skey, spid, n, inactive,
+                                                                               srec, cnt);
     return cudaGetLastError();
 }
 

@@ -120,12 +120,16 @@ __global__ void k_scan_add(uint32_t *a, int64_t n, const uint32_t *__restrict__ 
     for (int64_t k = i; k < min(n, (int64_t)(blockIdx.x + 1) * kScanChunk); k += blockDim.x) a[k] += s;
 }
 
-template <typename K>
+// kGather: the last pass of a sort whose values index a payload: instead of the keys and
+// values, write payload[value] to each element's slot (payload_out).
+template <typename K, bool kGather>
 __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const K *__restrict__ keys,
                                                                const uint32_t *__restrict__ vals, int64_t n,
                                                                int shift, int n_blocks,
                                                                const uint32_t *__restrict__ offs,
-                                                               K *keys_out, uint32_t *vals_out) {
+                                                               K *keys_out, uint32_t *vals_out,
+                                                               const float4 *__restrict__ payload,
+                                                               float4 *payload_out) {
     __shared__ uint32_t s_wc[kSortWarps][256];  // per warp: running count, then warp base
     __shared__ uint32_t s_off[256];             // output start of this CTA's digit d
     __shared__ uint32_t s_loc[256];             // start of digit d in the CTA's staged tile
@@ -206,9 +210,11 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const K *__restr
         s_dig[loc[r]] = (uint8_t)d;
     }
     __syncthreads();
-    for (int l = threadIdx.x; l < cnt; l += kSortThreads) {
-        const uint32_t d = s_dig[l];
-        keys_out[s_off[d] + (uint32_t)l - s_loc[d]] = s_key[l];
+    if (!kGather) {
+        for (int l = threadIdx.x; l < cnt; l += kSortThreads) {
+            const uint32_t d = s_dig[l];
+            keys_out[s_off[d] + (uint32_t)l - s_loc[d]] = s_key[l];
+        }
     }
     __syncthreads();
     uint32_t *s_val = reinterpret_cast<uint32_t *>(s_key);
@@ -220,7 +226,11 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const K *__restr
     __syncthreads();
     for (int l = threadIdx.x; l < cnt; l += kSortThreads) {
         const uint32_t d = s_dig[l];
-        vals_out[s_off[d] + (uint32_t)l - s_loc[d]] = s_val[l];
+        const uint32_t g = s_off[d] + (uint32_t)l - s_loc[d];
+        if (kGather)
+            payload_out[g] = payload[s_val[l]];
+        else
+            vals_out[g] = s_val[l];
     }
 }
 
@@ -236,9 +246,13 @@ size_t sort_temp_bytes(int64_t n) {
 // with the alternate buffers; *in_alt tells which pair of buffers holds the result.
 template <typename K>
 static cudaError_t sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int bit_lo,
-                             int bit_hi, void *temp, cudaStream_t st, bool *in_alt) {
+                             int bit_hi, void *temp, cudaStream_t st, bool *in_alt,
+                             const float4 *payload = nullptr, float4 *payload_out = nullptr) {
     *in_alt = false;
-    if (n <= 1) return cudaSuccess;
+    if (n <= 1 || bit_lo >= bit_hi) {
+        if (payload && n > 0) return launch_gather_records(payload, vals, n, payload_out, st);
+        return cudaSuccess;
+    }
     const int nb = sort_blocks(n);
     const int64_t h = (int64_t)256 * nb;
     const int chunks = (int)((h + kScanChunk - 1) / kScanChunk);
@@ -251,7 +265,12 @@ static cudaError_t sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *val
         k_scan_chunks<<<chunks, 1024, 0, st>>>(hist, h, sums);
         k_scan_sums<<<1, 1024, 0, st>>>(sums, chunks);
         k_scan_add<<<chunks, 1024, 0, st>>>(hist, h, sums);
-        k_digit_scatter<K><<<nb, kSortThreads, 0, st>>>(ka, va, n, shift, nb, hist, kb, vb);
+        if (payload && shift + 8 >= bit_hi)
+            k_digit_scatter<K, true><<<nb, kSortThreads, 0, st>>>(ka, va, n, shift, nb, hist, kb, vb, payload,
+                                                                 payload_out);
+        else
+            k_digit_scatter<K, false><<<nb, kSortThreads, 0, st>>>(ka, va, n, shift, nb, hist, kb, vb, nullptr,
+                                                                  nullptr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         std::swap(ka, kb);
@@ -269,6 +288,14 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                              int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt) {
     return sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, bit_lo, bit_hi, temp, st, in_alt);
+}
+
+cudaError_t radix_sort_gather(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                              int bit_lo, int bit_hi, void *temp, const float4 *payload, float4 *payload_out,
+                              cudaStream_t st) {
+    bool alt = false;
+    return sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, bit_lo, bit_hi, temp, st, &alt, payload,
+                               payload_out);
 }
 
 size_t scan_temp_bytes(int64_t n) {

@@ -1639,6 +1639,7 @@ extern "C" splotch_status splotch_render_ordered(splotch_scene *sc, const splotc
     const size_t o_map = cv.take(sizeof(float) * 6 * (size_t)rs.T * rs.T * (size_t)std::max(1, items));
     const size_t o_abs = cv.take(sizeof(float) * (size_t)sc->n_types);
     const size_t o_tmp = cv.take(std::max(sort_temp_bytes(std::max(n, Pm) + 1), scan_temp_bytes(n + 1)));
+    const size_t o_kr = cv.take(sizeof(uint32_t) * 2);
     char *var = (char *)sc->mem.alloc(fh.var_bytes, st);
     char *ex = var ? (char *)sc->mem.alloc(cv.off, st) : nullptr;
     if (!var || !ex) {
@@ -1655,15 +1656,31 @@ extern "C" splotch_status splotch_render_ordered(splotch_scene *sc, const splotc
     uint32_t *dka = (uint32_t *)(ex + o_dk0), *dkb = (uint32_t *)(ex + o_dk1);
     uint32_t *ida = (uint32_t *)(ex + o_id0), *idb = (uint32_t *)(ex + o_id1);
     bool alt = false;
+    uint32_t *krange = (uint32_t *)(ex + o_kr);
+    if (e == cudaSuccess) e = cudaMemsetAsync(krange, 0xFF, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(krange + 1, 0, sizeof(uint32_t), st);
     if (e == cudaSuccess)
-        e = launch_depth_records(sc->storage, sc->dev_view, fr.views, (float4 *)(ex + o_prec), dka, ida, st);
-    if (e == cudaSuccess) e = radix_sort_pairs(dka, dkb, ida, idb, sc->n, 0, 32, ex + o_tmp, st, &alt);
+        e = launch_depth_records(sc->storage, sc->dev_view, fr.views, (float4 *)(ex + o_prec), dka, ida, krange, st);
+    // sort only the bits the active depth keys span (relative to the smallest)
+    uint32_t kr[2] = {1u, 0u};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(kr, krange, sizeof(kr), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int dbits = 32;
+    uint32_t inactive = 0xFFFFFFFFu;  // the key of a particle that is not active
+    if (e == cudaSuccess && kr[0] <= kr[1] && kr[1] - kr[0] < 0xFFFFFFFEu) {
+        const uint32_t span = kr[1] - kr[0];
+        inactive = span + 1u;
+        dbits = 8;
+        while (dbits < 32 && ((uint64_t)span + 1u) >> dbits) dbits += 8;
+        e = launch_rebase_keys(dka, sc->n, kr[0], span, st);
+    }
+    if (e == cudaSuccess) e = radix_sort_pairs(dka, dkb, ida, idb, sc->n, 0, dbits, ex + o_tmp, st, &alt);
     if (alt) std::swap(dka, dkb), std::swap(ida, idb);
     // each particle's records at the scanned offsets of its tile counts, keyed by tile
     uint32_t *cnt = (uint32_t *)(ex + o_cnt);
     if (e == cudaSuccess)
-        e = launch_sorted_counts(fr.views, (const float4 *)(ex + o_prec), dka, ida, sc->n, (float4 *)(ex + o_srec),
-                                 cnt, st);
+        e = launch_sorted_counts(fr.views, (const float4 *)(ex + o_prec), dka, ida, sc->n, inactive,
+                                 (float4 *)(ex + o_srec), cnt, st);
     if (e == cudaSuccess) e = exclusive_scan_u32(cnt, sc->n + 1, ex + o_tmp, st);
     uint32_t *tka = (uint32_t *)(ex + o_tk0), *tkb = (uint32_t *)(ex + o_tk1);
     uint32_t *tva = (uint32_t *)(ex + o_tv0), *tvb = (uint32_t *)(ex + o_tv1);
@@ -1673,9 +1690,8 @@ extern "C" splotch_status splotch_render_ordered(splotch_scene *sc, const splotc
     // stable by tile id: every tile list keeps depth order
     int tbits = 8;
     while (tbits < 32 && ((int64_t)(rs.views[0].n_tiles - 1) >> tbits) > 0) tbits += 8;
-    if (e == cudaSuccess) e = radix_sort_pairs(tka, tkb, tva, tvb, P, 0, tbits, ex + o_tmp, st, &alt);
-    if (alt) std::swap(tka, tkb), std::swap(tva, tvb);
-    if (e == cudaSuccess) e = launch_gather_records((const float4 *)(ex + o_rec), tva, P, fr.lists, st);
+    if (e == cudaSuccess)
+        e = radix_sort_gather(tka, tkb, tva, tvb, P, 0, tbits, ex + o_tmp, (const float4 *)(ex + o_rec), fr.lists, st);
     const int64_t squares = (int64_t)std::max(1, items) * split * split;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count(sc->dev) * ordered_ctas_per_sm(),
                                                                 (squares + 3) / 4));

@@ -307,18 +307,26 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
                              int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt);
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                              int bit_lo, int bit_hi, void *temp, cudaStream_t st, bool *in_alt);
+// Sort by key bits [bit_lo, bit_hi) whose values index `payload`, and write the payload in
+// sorted order to payload_out (the last pass gathers; keys and values end up undefined).
+cudaError_t radix_sort_gather(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                              int bit_lo, int bit_hi, void *temp, const float4 *payload, float4 *payload_out,
+                              cudaStream_t st);
 // In-place exclusive scan of 32-bit counts whose total stays below 2^32.
 size_t scan_temp_bytes(int64_t n);
 cudaError_t exclusive_scan_u32(uint32_t *a, int64_t n, void *temp, cudaStream_t st);
 
-// Depth-ordered binning of one view (views[0]): per-particle records and depth keys, the
+// Depth-ordered binning of one view (views[0]): per-particle records and depth keys (with
+// the range of the active keys, and their rebasing to it), the
 // counts in sorted order (cnt has n + 1 entries, the last set to 0), and the expansion
 // into (tile id, slot) pairs at the scanned offsets; k_expand flags kStatOverflow in
 // `status` if a particle's tiles disagree with its count.
 cudaError_t launch_depth_records(int storage, const SceneDev &sc, const ViewParams *views, float4 *prec,
-                                 uint32_t *dkey, uint32_t *pid, cudaStream_t st);
+                                 uint32_t *dkey, uint32_t *pid, uint32_t *krange, cudaStream_t st);
+cudaError_t launch_rebase_keys(uint32_t *dkey, int64_t n, uint32_t base, uint32_t span, cudaStream_t st);
 cudaError_t launch_sorted_counts(const ViewParams *views, const float4 *prec, const uint32_t *skey,
-                                 const uint32_t *spid, int64_t n, float4 *srec, uint32_t *cnt, cudaStream_t st);
+                                 const uint32_t *spid, int64_t n, uint32_t inactive, float4 *srec, uint32_t *cnt,
+                                 cudaStream_t st);
 cudaError_t launch_expand(const ViewParams *views, const float4 *srec, const uint32_t *poff, int64_t n, int64_t P,
                           float4 *recs, uint32_t *tkey, uint32_t *tval, int *status, cudaStream_t st);
 
