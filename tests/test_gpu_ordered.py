@@ -165,6 +165,45 @@ def test_ordered_equal_depths_apply_in_index_order(tile):
     assert np.abs(got - ref).max() <= TOL_O["f32"]
 
 
+def test_ordered_degenerate_scenes():
+    """No particles, every particle behind the camera, and a single particle: the ordered
+    render writes a black image, or the one particle's closed form (I = (E/A)(1 - e^-A w)
+    per pixel, from the oracle), over the whole (ragged) image."""
+    import oracle_pins as P
+    cam = synth.front_camera(77, 53)
+    absorb = [1.3]
+    empty = P.make_set(np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0))
+    out = torch.full((53, 77, 3), float("nan"), device="cuda")
+    got = render.Scene(empty, "f32").render_ordered(cam, absorb, out=out).cpu().numpy()
+    assert np.array_equal(got, np.zeros_like(got))
+    behind = P.make_set([0.5] * 50, [0.5] * 50, np.linspace(3.0, 4.0, 50), [0.01] * 50)
+    out.fill_(float("nan"))
+    got = render.Scene(behind, "f32").render_ordered(cam, absorb, out=out).cpu().numpy()
+    assert np.array_equal(got, np.zeros_like(got))
+    one = P.make_set([0.5], [0.52], [0.5], [0.02], [0.7], beta=0.4)
+    ref = oracle.render_rt_depth(one, cam, absorb)
+    got = render.Scene(one, "f32").render_ordered(cam, absorb, render.RenderParams(tile=8)).cpu().numpy()
+    assert ref.max() > 0.05 and np.abs(got - ref).max() <= 1e-5
+
+
+def test_ordered_one_crowded_tile_many_slices():
+    """Forty thousand particles on one tile: its list is cut into many slices whose maps
+    compose far to near; also the tile of 32 px rendered as four squares."""
+    import oracle_pins as P
+    rng = np.random.default_rng(8)
+    n = 40000
+    cm = np.array([[0.2, 0.5, 0.9], [0.9, 0.4, 0.1]], np.float32)
+    ps = P.make_set(0.5 + 0.002 * rng.standard_normal(n), 0.5 + 0.002 * rng.standard_normal(n),
+                    rng.uniform(0.3, 0.7, n), np.full(n, 0.001), rng.uniform(0, 1, n),
+                    type_begin=[0, n // 2, n], cmaps=[cm, cm[::-1].copy()], betas=[0.01, 0.02])
+    cam = synth.front_camera(70, 70)
+    absorb = [3.0, 0.5]
+    ref = oracle.render_rt_depth(ps, cam, absorb)
+    for tile in (16, 32):
+        got = render.Scene(ps, "f32").render_ordered(cam, absorb, render.RenderParams(tile=tile)).cpu().numpy()
+        assert np.abs(got - ref).max() <= TOL_O["f32"], tile
+
+
 def test_ordered_rejects_large_tiles_and_bad_absorption():
     sc = render.Scene(_species_set(30, 2000, 500), "f32")
     cam = synth.front_camera(128, 128)
