@@ -313,3 +313,25 @@ def test_plan_per_view_colormaps_match_the_oracle():
     assert e.value.status == _lib.UNSUPPORTED
     pv.close()
     sv.close()
+
+
+def test_plan_per_view_colormaps_with_cta_tiles():
+    """Per-view colormaps through the CTA kernel (tiles above 32 px read the view's table
+    at run time), against the oracle per view."""
+    import oracle
+    ps = synth.two_species_set(20000, 8000, 19, grid=32).with_brightness([0.05, 0.3])
+    cams = synth.orbit_cameras(2, 120, 100)
+    rng = np.random.default_rng(4)
+    maps = [[synth.smooth_ramp_cmap(rng, n=int(rng.integers(2, 100))) for _ in range(2)] for _ in range(2)]
+    sc = render.Scene(ps, "f32")
+    plan = render.Plan(sc, cams, render.RenderParams(tile=40))
+    plan.set_colormaps(maps)
+    out = plan.new_output()
+    plan.launch(out)
+    plan.check()
+    for v, cam in enumerate(cams):
+        pv = ps.with_brightness(ps.brightness)
+        pv.cmaps = maps[v]
+        assert np.abs(out[v].cpu().numpy() - oracle.final(oracle.render(pv, cam))).max() <= 1e-4, v
+    plan.close()
+    sc.close()

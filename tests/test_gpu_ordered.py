@@ -165,6 +165,18 @@ def test_ordered_equal_depths_apply_in_index_order(tile):
     assert np.abs(got - ref).max() <= TOL_O["f32"]
 
 
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_ordered_reduced_precision_storage(storage):
+    """The ordered render of a scene stored in BF16 / FP16, against the oracle fed the same
+    rounded attributes (bar 2e-3)."""
+    ps = _species_set(50)
+    cam = synth.front_camera(150, 120)
+    absorb = [2.0, 0.3]
+    ref = oracle.render_rt_depth(ps, cam, absorb, storage=storage)
+    got = render.Scene(ps, storage).render_ordered(cam, absorb, render.RenderParams(tile=24)).cpu().numpy()
+    assert np.abs(got - ref).max() <= 2e-3, storage
+
+
 def test_ordered_degenerate_scenes():
     """No particles, every particle behind the camera, and a single particle: the ordered
     render writes a black image, or the one particle's closed form (I = (E/A)(1 - e^-A w)

@@ -4,7 +4,7 @@ input field, or from a scalar through a colormap) against the FP64 oracle (needs
 A scene with a vector-coloured species holds a per-particle emission and its tile records
 carry particle indices; every splat kernel reads the emission through them.  The cases
 cover the warp kernel at both square sizes and the quadrant split (tiles 8, 16, 24, 32),
-the CTA kernel (tile 40), FP16 storage, a plan with a per-view brightness sequence, the
+the CTA kernel (tile 40), FP16 and BF16 storage, a plan with a per-view brightness sequence, the
 depth-ordered render, the out-of-core render (colour ranges over the whole set) and the
 argument checks."""
 import numpy as np
@@ -16,7 +16,7 @@ from paper_1606_04427_gb300 import _lib, build, render, synth
 
 pytestmark = pytest.mark.gpu
 
-TOL_O = {"f32": 1e-4, "f16": 2e-3}
+TOL_O = {"f32": 1e-4, "f16": 2e-3, "bf16": 2e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,7 +30,8 @@ def _vector_set(seed, n_gas=40000, n_star=15000, species=(1,)):
     return synth.with_vector_colour(ps, species, seed)
 
 
-@pytest.mark.parametrize("tile,storage", [(8, "f32"), (16, "f32"), (24, "f16"), (32, "f32"), (40, "f32")])
+@pytest.mark.parametrize("tile,storage", [(8, "f32"), (16, "f32"), (16, "bf16"), (24, "f16"), (32, "f32"),
+                                          (40, "f32")])
 def test_vector_colour_matches_the_oracle(tile, storage):
     ps = _vector_set(10 + tile)
     cam = synth.front_camera(200, 150)
