@@ -52,7 +52,7 @@ def _bind(path: str):
     P = C.c_void_p
     i64, i32, f32, f64 = C.c_int64, C.c_int, C.c_float, C.c_double
     scene = [i64, P, P, P, P, P, i32, P, P, P, P, P, P, i32, i32, f32, f32, f64, P, P]
-    lib.orc_camera.argtypes = [P, P, P, f64, f64, i32, i32, P, P]
+    lib.orc_camera.argtypes = [P, P, P, f64, f64, f64, i32, i32, P, P]
     lib.orc_camera.restype = i32
     lib.orc_normalise.argtypes = [i64, P, i32, i32, f64, f64, i32, P]
     lib.orc_quantise_f32.argtypes = [i64, P, P, i32]
@@ -71,6 +71,8 @@ def _bind(path: str):
     lib.orc_render_rt_depth.argtypes = scene + [P, P]
     lib.orc_render_rt_depth.restype = i32
     lib.orc_render_rt_depth_lattice.argtypes = scene + [P, i32, i32, i32, P]
+    lib.orc_render_rt_depth_map.argtypes = scene + [P, P, P]
+    lib.orc_render_rt_depth_map.restype = i32
     lib.orc_render_rt_depth_lattice.restype = i32
     lib.orc_count_work.argtypes = scene + [i32, P]
     lib.orc_count_work.restype = i32
@@ -154,15 +156,16 @@ class Params:
 
 
 def camera(cam):
-    """FP32 3x4 view matrix and {F, cx, cy, z_near}; raises ValueError when rejected."""
+    """FP32 3x4 view matrix and {F, cx, cy, z_near, z_far}; raises ValueError when rejected.
+    A camera without z_far (or with z_far 0 / infinite) has no far plane."""
     lib = _cur()
     m = np.zeros(12, np.float32)
-    p = np.zeros(4, np.float32)
+    p = np.zeros(5, np.float32)
     e = np.asarray(cam.eye, np.float64)
     l = np.asarray(cam.lookat, np.float64)
     u = np.asarray(cam.up, np.float64)
     rc = lib.orc_camera(_ptr(e), _ptr(l), _ptr(u), float(cam.fov_deg), float(cam.z_near),
-                        int(cam.width), int(cam.height), _ptr(m), _ptr(p))
+                        float(getattr(cam, "z_far", 0.0) or 0.0), int(cam.width), int(cam.height), _ptr(m), _ptr(p))
     if rc != 0:
         raise ValueError("camera rejected")
     return m, p
@@ -294,6 +297,18 @@ def render_rt_depth(ps, cam, absorb, params: Params = Params(), storage: str = "
     rc = _cur().orc_render_rt_depth(*s.args(), _ptr(ab), _ptr(I))
     assert rc == 0
     return I
+
+
+def render_rt_depth_map(ps, cam, absorb, params: Params = Params(), storage: str = "f32"):
+    """(alpha, beta), each H x W x 3 FP64: the depth-ordered transfer as the affine map
+    I_out = alpha I_in + beta it applies to each pixel (beta = render_rt_depth)."""
+    s = _Scene(ps, cam, params, storage)
+    ab = np.ascontiguousarray(np.broadcast_to(np.asarray(absorb, np.float64), (s.nt,)))
+    A = np.ones((s.H, s.W, 3), np.float64)
+    B = np.zeros((s.H, s.W, 3), np.float64)
+    rc = _cur().orc_render_rt_depth_map(*s.args(), _ptr(ab), _ptr(A), _ptr(B))
+    assert rc == 0
+    return A, B
 
 
 def render_rt_depth_lattice(ps, cam, absorb, stride: int, ox: int = 0, oy: int = 0, params: Params = Params(),

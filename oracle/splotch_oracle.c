@@ -79,9 +79,11 @@ static void cross3(const double a[3], const double b[3], double o[3])
 }
 
 int orc_camera(const double eye[3], const double look[3], const double up[3], double fov_deg,
-               double z_near, int W, int H, float m[12], float p[4])
+               double z_near, double z_far, int W, int H, float m[12], float p[5])
 {
     if (W < 1 || H < 1 || !(fov_deg > 0.0 && fov_deg < 180.0) || !(z_near > 0.0)) return ORC_EINVAL;
+    const int has_far = z_far > 0.0 && isfinite(z_far);
+    if (has_far && !(z_far > z_near)) return ORC_EINVAL;
     double d[3] = {look[0] - eye[0], look[1] - eye[1], look[2] - eye[2]};
     double nd = sqrt(dot3(d, d));
     if (!(nd > 0.0)) return ORC_EINVAL;
@@ -104,6 +106,7 @@ int orc_camera(const double eye[3], const double look[3], const double up[3], do
     p[1] = 0.5f * (float)W;
     p[2] = 0.5f * (float)H;
     p[3] = (float)z_near;
+    p[4] = has_far ? (float)z_far : INFINITY;
     return ORC_OK;
 }
 
@@ -181,7 +184,7 @@ void orc_normalise(int64_t n, const float *I, int i_log, int range_given, double
  *
  * FP32, each operation rounded once, left to right:
  *   xc = ((m0 x + m1 y) + m2 z) + m3,  yc and zc likewise with rows 1 and 2
- *   visible iff zc > zn
+ *   visible iff zn < zc <= zf (zf: the far plane, +infinity when there is none)
  *   X = cx + (F xc) / zc;  Y = cy - (F yc) / zc;  r = (F h) / zc
  *   R = rfac r, raised to rmin when below it
  *   active iff visible, X, Y, R finite, and the pixel box below is not empty
@@ -196,18 +199,18 @@ typedef struct {
     int active;
 } orc_px;
 
-static void raster_one(float x, float y, float z, float h, const float m[12], const float p[4],
+static void raster_one(float x, float y, float z, float h, const float m[12], const float p[5],
                        int W, int H, float rfac, float rmin, orc_px *o)
 {
     float xc = ((m[0] * x + m[1] * y) + m[2] * z) + m[3];
     float yc = ((m[4] * x + m[5] * y) + m[6] * z) + m[7];
     float zc = ((m[8] * x + m[9] * y) + m[10] * z) + m[11];
-    float F = p[0], cx = p[1], cy = p[2], zn = p[3];
+    float F = p[0], cx = p[1], cy = p[2], zn = p[3], zf = p[4];
     memset(o, 0, sizeof(*o));
     o->zc = zc;
     o->i0 = o->j0 = 0;
     o->i1 = o->j1 = -1;
-    if (!(zc > zn)) return;
+    if (!(zc > zn) || !(zc <= zf)) return;
     float X = cx + (F * xc) / zc;
     float Y = cy - (F * yc) / zc;
     float r = (F * h) / zc;
@@ -293,7 +296,7 @@ typedef struct {
     const float *const *cmap;
     const int *cmap_len;
     const double *beta;
-    float m[12], p[4];
+    float m[12], p[5];
     int W, H;
     float rfac, rmin;
     double sor;
@@ -329,7 +332,7 @@ static orc_px *raster_all(const orc_scene *s, double (*ecol)[3])
 static void fill_scene(orc_scene *s, int64_t n, const float *x, const float *y, const float *z,
                        const float *h, const double *It, int n_types, const int64_t *type_begin,
                        const float *const *cmap, const int *cmap_len, const double *beta,
-                       const float m[12], const float p[4], int W, int H, float rfac, float rmin,
+                       const float m[12], const float p[5], int W, int H, float rfac, float rmin,
                        double sor, const double *rgb, const int *vec)
 {
     s->rgb = rgb;
@@ -351,7 +354,7 @@ static void fill_scene(orc_scene *s, int64_t n, const float *x, const float *y, 
 #define SCENE_ARGS                                                                                 \
     int64_t n, const float *x, const float *y, const float *z, const float *h, const double *It,   \
         int n_types, const int64_t *type_begin, const float *const *cmap, const int *cmap_len,     \
-        const double *beta, const float m[12], const float p[4], int W, int H, float rfac,         \
+        const double *beta, const float m[12], const float p[5], int W, int H, float rfac,         \
         float rmin, double sor, const double *rgb, const int *vec
 #define SCENE_PASS n, x, y, z, h, It, n_types, type_begin, cmap, cmap_len, beta, m, p, W, H, rfac, rmin, sor, rgb, vec
 
@@ -489,7 +492,7 @@ static int by_depth(const void *pa, const void *pb)
  * particles that cover it, so the particles whose box holds no lattice pixel are left out
  * before the depth sort; the rest are applied in the same order, so each lattice pixel
  * equals the full image's pixel exactly.  For checks of images too large to render whole. */
-int orc_render_rt_depth_lattice(SCENE_ARGS, const double *absorb, int ox, int oy, int stride, double *L)
+static int rt_depth_lattice(SCENE_ARGS, const double *absorb, int ox, int oy, int stride, double *L, double *Amap)
 {
     if (stride < 1 || ox < 0 || oy < 0 || ox >= W || oy >= H) return 1;
     const int nx = (W - ox + stride - 1) / stride, ny = (H - oy + stride - 1) / stride;
@@ -511,6 +514,8 @@ int orc_render_rt_depth_lattice(SCENE_ARGS, const double *absorb, int ox, int oy
     g_sort_px = px;
     qsort(ord, (size_t)na, sizeof(int64_t), by_depth);
     memset(L, 0, sizeof(double) * 3 * (size_t)nx * (size_t)ny);
+    if (Amap)
+        for (size_t k = 0; k < 3 * (size_t)nx * (size_t)ny; ++k) Amap[k] = 1.0;
     for (int64_t q = 0; q < na; ++q) {
         const int64_t k = ord[q];
         const orc_px *o = &px[k];
@@ -528,6 +533,7 @@ int orc_render_rt_depth_lattice(SCENE_ARGS, const double *absorb, int ox, int oy
                     if (A > 0.0) {
                         double t = exp(-A * w);
                         v[c] = v[c] * t + (E / A) * (1.0 - t);
+                        if (Amap) Amap[3 * ((size_t)b * nx + a) + c] *= t;
                     } else {
                         v[c] = v[c] + E * w;
                     }
@@ -540,11 +546,26 @@ int orc_render_rt_depth_lattice(SCENE_ARGS, const double *absorb, int ox, int oy
     return ORC_OK;
 }
 
+int orc_render_rt_depth_lattice(SCENE_ARGS, const double *absorb, int ox, int oy, int stride, double *L)
+{
+    return rt_depth_lattice(SCENE_PASS, absorb, ox, oy, stride, L, NULL);
+}
+
 /* The whole image: the lattice of stride 1. */
 int orc_render_rt_depth(SCENE_ARGS, const double *absorb, double *I)
 {
     if (W <= 0 || H <= 0) return ORC_OK;
-    return orc_render_rt_depth_lattice(SCENE_PASS, absorb, 0, 0, 1, I);
+    return rt_depth_lattice(SCENE_PASS, absorb, 0, 0, 1, I, NULL);
+}
+
+/* The same transfer as the affine map it applies to a pixel's incoming intensity:
+ * I_out = alpha I_in + beta per channel, beta = the image above (black background) and
+ * alpha = the product of exp(-A w) over the particles covering the pixel (1 where none
+ * absorbs).  Maps of consecutive depth slabs compose far to near. */
+int orc_render_rt_depth_map(SCENE_ARGS, const double *absorb, double *map_alpha, double *map_beta)
+{
+    if (W <= 0 || H <= 0) return ORC_OK;
+    return rt_depth_lattice(SCENE_PASS, absorb, 0, 0, 1, map_beta, map_alpha);
 }
 
 /* Brute force: every pixel against every particle, no box and no tiles; coverage is the
@@ -562,7 +583,8 @@ int orc_render_bruteforce(SCENE_ARGS, double *a)
             q[0] = q[1] = q[2] = 0.0;
             for (int64_t k = 0; k < n; ++k) {
                 const orc_px *o = &px[k];
-                if (!(o->zc > p[3]) || !(isfinite(o->X) && isfinite(o->Y) && isfinite(o->R))) continue;
+                if (!(o->zc > p[3]) || !(o->zc <= p[4]) || !(isfinite(o->X) && isfinite(o->Y) && isfinite(o->R)))
+                    continue;
                 if (!covered(o, i, j)) continue;
                 double w = weight(o, i, j, sor);
                 for (int c = 0; c < 3; ++c) q[c] += e[k][c] * w;

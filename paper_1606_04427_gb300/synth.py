@@ -27,7 +27,8 @@ CENTRE = (0.5, 0.5, 0.5)
 @dataclass
 class Camera:
     """Pinhole camera: eye and look-at positions, up hint, vertical field of
-    view in degrees, near-plane distance (world units) and image size."""
+    view in degrees, near-plane distance (world units), image size, and an optional
+    far-plane distance (0: none)."""
     eye: Sequence[float]
     lookat: Sequence[float]
     up: Sequence[float] = (0.0, 1.0, 0.0)
@@ -35,6 +36,7 @@ class Camera:
     z_near: float = 1e-3
     width: int = 256
     height: int = 256
+    z_far: float = 0.0
 
 
 @dataclass

@@ -161,6 +161,41 @@ def pin_near_plane_cull():
     assert not r["active"][0] and not r["active"][1] and r["active"][3]
 
 
+def pin_far_plane_cull():
+    """The far plane keeps z_c <= z_far (inclusive) and culls beyond; with no far plane
+    (0 or infinite) nothing is culled for distance; z_far <= z_near is rejected."""
+    z = [0.5, 0.49, 0.51, -3.0, 2.0]  # z_c = 2.5 - z: 2.0 exactly, 2.01, 1.99, 5.5, 0.5
+    ps = make_set([0.5] * 5, [0.5] * 5, z, [0.001] * 5)
+    cam = front(64, 64, dist=2.0)
+    r = oracle.raster(ps, cam)
+    assert r["zc"][0] == np.float32(2.0) and list(r["active"]) == [True] * 5
+    cam.z_far = 2.0
+    assert list(oracle.raster(ps, cam)["active"]) == [True, False, True, False, True]
+    cam.z_far = float("inf")
+    assert list(oracle.raster(ps, cam)["active"]) == [True] * 5
+    cam.z_far = cam.z_near
+    try:
+        oracle.camera(cam)
+        raise AssertionError("z_far <= z_near accepted")
+    except ValueError:
+        pass
+
+
+def pin_depth_slabs_partition_the_particles():
+    """Cameras that differ only in (z_near, z_far) = consecutive slab bounds make each
+    active particle active in exactly one slab."""
+    rng = np.random.default_rng(2)
+    n = 5000
+    ps = make_set(rng.uniform(0, 1, n), rng.uniform(0, 1, n), rng.uniform(0, 1, n), np.full(n, 0.004))
+    bounds = [1e-3, 1.7, 2.0, 2.0001, 2.3, 0.0]
+    seen = np.zeros(n, np.int64)
+    for lo, hi in zip(bounds[:-1], bounds[1:]):
+        cam = front(96, 96, dist=2.0, z_near=lo)
+        cam.z_far = hi
+        seen += oracle.raster(ps, cam)["active"]
+    assert np.array_equal(seen, oracle.raster(ps, front(96, 96, dist=2.0))["active"].astype(np.int64))
+
+
 # ----------------------------------------------------------------------------------------
 # Gaussian footprint (Section 2.1) and additive drawing (Section 3.2.2)
 
@@ -460,6 +495,33 @@ def pin_rt_depth_equal_depths_in_index_order():
         want = I0 * np.exp(-A1) + (e[1] / A1) * (1.0 - np.exp(-A1))
         got = oracle.render_rt_depth(ps, front(W, H), s_abs)[40, 20]
         assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max(), (betas, got, want)
+
+
+def pin_rt_depth_map_closed_forms_and_slab_composition():
+    """The transfer as an affine map: with unit absorption alpha = exp(-a) and beta =
+    1 - exp(-a) (a the direct render's accumulation); with zero absorption alpha = 1 and
+    beta = a; and the maps of two depth slabs (cameras with near / far planes at a split
+    depth) compose far to near into the whole image: I = alpha_near beta_far + beta_near."""
+    rng = np.random.default_rng(9)
+    n = 4000
+    cm = np.array([[0.2, 0.5, 0.9], [0.9, 0.4, 0.1]], np.float32)
+    ps = make_set(rng.uniform(0.3, 0.7, n), rng.uniform(0.3, 0.7, n), rng.uniform(0.2, 0.8, n),
+                  np.exp(rng.uniform(np.log(0.004), np.log(0.03), n)), rng.uniform(0, 1, n),
+                  type_begin=[0, n // 2, n], cmaps=[cm, cm[::-1].copy()], betas=[0.05, 0.2])
+    cam = front(90, 70)
+    a = oracle.render(ps, cam)
+    A1, B1 = oracle.render_rt_depth_map(ps, cam, [1.0, 1.0])
+    assert np.abs(A1 - np.exp(-a)).max() <= 1e-12 and np.abs(B1 - (1.0 - np.exp(-a))).max() <= 1e-12
+    A0, B0 = oracle.render_rt_depth_map(ps, cam, [0.0, 0.0])
+    assert np.array_equal(A0, np.ones_like(A0)) and np.abs(B0 - a).max() <= 1e-12
+    absorb = [2.5, 0.4]
+    whole = oracle.render_rt_depth(ps, cam, absorb)
+    near, far = front(90, 70), front(90, 70, z_near=2.05)
+    near.z_far = 2.05
+    An, Bn = oracle.render_rt_depth_map(ps, near, absorb)
+    Af, Bf = oracle.render_rt_depth_map(ps, far, absorb)
+    assert np.abs(Af - 1.0).max() > 0.05 and np.abs(An - 1.0).max() > 0.05  # both slabs absorb
+    assert np.abs(An * Bf + Bn - whole).max() <= 1e-12
 
 
 def pin_rt_depth_lattice_is_the_full_image_restricted():

@@ -23,7 +23,9 @@ MUTANTS = {
                          "m[4 * r + 3] = (float)(dot3(rows[r], eye));"),
     "radius_no_depth": ("float r = (F * h) / zc;", "float r = F * h;"),
     "radius_no_floor": ("if (!(R > rmin)) R = rmin;", ""),
-    "near_plane_ignored": ("if (!(zc > zn)) return;", "if (!(zc > 0.0f)) return;"),
+    "near_plane_ignored": ("if (!(zc > zn) || !(zc <= zf)) return;", "if (!(zc > 0.0f) || !(zc <= zf)) return;"),
+    "far_plane_exclusive": ("if (!(zc > zn) || !(zc <= zf)) return;", "if (!(zc > zn) || !(zc < zf)) return;"),
+    "far_plane_ignored": ("if (!(zc > zn) || !(zc <= zf)) return;", "if (!(zc > zn)) return;"),
     "box_too_narrow": ("int i0 = (int)ceilf(xl) - 1, i1 = (int)floorf(xh) + 1;",
                        "int i0 = (int)ceilf(xl) + 1, i1 = (int)floorf(xh) - 1;"),
     "coverage_wrong_operand": ("float d2 = dx * dx + dy * dy;", "float d2 = dx * dx + dx * dy;"),
@@ -40,6 +42,8 @@ MUTANTS = {
     "rt_depth_one_species": ("const double st = absorb[type_of(&s, k)];", "const double st = absorb[0];"),
     "rt_depth_emission_over_absorption_dropped": ("v[c] = v[c] * t + (E / A) * (1.0 - t);",
                                                   "v[c] = v[c] * t + (1.0 - t);"),
+    "rt_map_alpha_not_multiplied": ("if (Amap) Amap[3 * ((size_t)b * nx + a) + c] *= t;",
+                                    "if (Amap) Amap[3 * ((size_t)b * nx + a) + c] = t;"),
     "vector_colour_ignored": ("if (s->vec && s->vec[t])", "if (0 && s->vec)"),
     "vector_components_swapped": ("for (int c = 0; c < 3; ++c) e[c] = beta * rgb[c];",
                                   "for (int c = 0; c < 3; ++c) e[c] = beta * rgb[2 - c];"),
