@@ -116,16 +116,21 @@ typedef struct {
     const float *rgb;
 } splotch_scene_desc;
 
-/* Camera (Section 2.1: supplied camera and look-at positions).  FP64 on the host; the
- * library composes f = (L - E)/|L - E|, s = (f x U)/|f x U|, u = s x f, rows (s, u, f)
- * with translations -(row . E), and F = (0.5 H) / tan(fov_deg pi / 360), then rounds
- * each to FP32 (the only FP64 step).  Rejected: width or height < 1, fov outside
- * (0, 180), z_near <= 0, eye == lookat, |f x U| <= 1e-9 |U|. */
+/* Camera (Section 2.1: supplied camera and look-at positions, then clipping).  FP64 on
+ * the host; the library composes f = (L - E)/|L - E|, s = (f x U)/|f x U|, u = s x f,
+ * rows (s, u, f) with translations -(row . E), and F = (0.5 H) / tan(fov_deg pi / 360),
+ * then rounds each to FP32 (the only FP64 step).  A particle is visible for
+ * z_near < zc <= z_far (FP32 zc and planes); z_far 0 or not finite: no far plane.
+ * Cameras that differ only in (z_near, z_far) = consecutive bounds cut the particles
+ * into depth slabs, each particle in exactly one.  Rejected: width or height < 1, fov
+ * outside (0, 180), z_near <= 0, a far plane at or before z_near, eye == lookat,
+ * |f x U| <= 1e-9 |U|. */
 typedef struct {
     double eye[3], lookat[3], up[3];
     double fov_deg; /* vertical field of view, degrees */
     double z_near;  /* particles with camera depth <= z_near are culled */
     int32_t width, height;
+    double z_far;   /* particles with camera depth > z_far are culled; 0: no far plane */
 } splotch_camera;
 
 /* Render parameters.
@@ -158,7 +163,10 @@ typedef struct {
     int32_t flags;
 } splotch_render_params;
 
-enum { SPLOTCH_OUT_ACCUM = 1, SPLOTCH_SYNC = 2, SPLOTCH_PLAN_GRAPH = 4, SPLOTCH_TIMING = 8, SPLOTCH_OUT_ADD = 16 };
+enum {
+    SPLOTCH_OUT_ACCUM = 1, SPLOTCH_SYNC = 2, SPLOTCH_PLAN_GRAPH = 4, SPLOTCH_TIMING = 8, SPLOTCH_OUT_ADD = 16,
+    SPLOTCH_OUT_MAP = 32  /* splotch_render_ordered: write the per-pixel affine map (alpha, beta) */
+};
 
 /* Defaults listed above. */
 splotch_render_params splotch_default_params(void);
@@ -177,12 +185,12 @@ splotch_status splotch_scene_info(const splotch_scene *scene, int64_t *n, int32_
                                   int32_t *storage, int64_t *device_bytes);
 
 /* The FP32 camera parameters the kernels use: m = 3x4 row-major view matrix,
- * p = {F, W/2, H/2, z_near}.  Host only. */
-splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], float p[4]);
+ * p = {F, W/2, H/2, z_near, z_far (+infinity without a far plane)}.  Host only. */
+splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], float p[5]);
 
 /* Render n_views >= 1 frames of one scene into out (device, n_views x H x W x 3 FP32; all
  * cameras the same size).  Per view, per particle (FP32, each operation rounded once):
- *   xc = ((m0 x + m1 y) + m2 z) + m3 (rows 1, 2 likewise), visible iff zc > z_near;
+ *   xc = ((m0 x + m1 y) + m2 z) + m3 (rows 1, 2 likewise), visible iff z_near < zc <= z_far;
  *   X = W/2 + (F xc)/zc, Y = H/2 - (F yc)/zc, r = (F h)/zc, R = max(rfac r, r_min_px);
  *   pixel box i in [max(0, ceil(clamp((X - R) - 0.5, -2, W + 1)) - 1),
  *                   min(W - 1, floor(clamp((X + R) - 0.5, -2, W + 1)) + 1)], rows likewise;
@@ -203,8 +211,13 @@ splotch_status splotch_render(splotch_scene *scene, const splotch_camera *cams, 
  * are applied from the farthest to the nearest (z_c descending) from a black background:
  * I <- I exp(-A w) + (E / A)(1 - exp(-A w)), or I <- I + E w where A = 0.  out: device,
  * H x W x 3 FP32, receives I (no final transform: with absorb[t] = 1 for every species I
- * equals 1 - exp(-a) of splotch_render).  Particles at exactly equal depth are applied in
- * index order.  Tiles up to 32 px (larger: UNSUPPORTED).  The particles are sorted by
+ * equals 1 - exp(-a) of splotch_render).  With SPLOTCH_OUT_MAP in params->flags, out is
+ * H x W x 6 and receives, per pixel, the affine map the particles apply to the intensity
+ * entering from behind, I_out = alpha I_in + beta: (alpha_r, alpha_g, alpha_b, beta_r,
+ * beta_g, beta_b), alpha the product of exp(-A w) and beta the I above; the maps of
+ * depth slabs (cameras with consecutive near / far planes) compose far to near into the
+ * whole frame.  Particles at exactly equal depth are applied in index order.  Tiles up
+ * to 32 px (larger: UNSUPPORTED); other output flags are ignored.  The particles are sorted by
  * depth (stable radix sort from index order), their records written out in that order and
  * grouped by a stable sort on tile id; device memory besides the tile lists: about 52
  * bytes per particle and 32 per particle-tile pair.  Synchronous.  Errors: INVALID_ARG,

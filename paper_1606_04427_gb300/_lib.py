@@ -15,7 +15,7 @@ from . import build as _build
 OK, INVALID_ARG, OOM, CUDA, CAPACITY, TIMEOUT, UNSUPPORTED = range(7)
 F32, F16, BF16 = 0, 1, 2
 STORAGE = {"f32": F32, "f16": F16, "bf16": BF16}
-OUT_ACCUM, SYNC, PLAN_GRAPH, TIMING, OUT_ADD = 1, 2, 4, 8, 16
+OUT_ACCUM, SYNC, PLAN_GRAPH, TIMING, OUT_ADD, OUT_MAP = 1, 2, 4, 8, 16, 32
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -38,7 +38,7 @@ class SceneDesc(C.Structure):
 class CameraC(C.Structure):
     _fields_ = [("eye", C.c_double * 3), ("lookat", C.c_double * 3), ("up", C.c_double * 3),
                 ("fov_deg", C.c_double), ("z_near", C.c_double), ("width", C.c_int32),
-                ("height", C.c_int32)]
+                ("height", C.c_int32), ("z_far", C.c_double)]
 
 
 class RenderParamsC(C.Structure):
@@ -132,6 +132,7 @@ def camera_c(cam) -> CameraC:
     c.up[:] = [float(v) for v in cam.up]
     c.fov_deg = float(cam.fov_deg)
     c.z_near = float(cam.z_near)
+    c.z_far = float(getattr(cam, "z_far", 0.0) or 0.0)
     c.width = int(cam.width)
     c.height = int(cam.height)
     return c

@@ -127,7 +127,7 @@ __device__ __forceinline__ void apply_record(const float4 &pa, const float4 &pk,
 
 __global__ void __launch_bounds__(kOWarps * 32, 4)
     k_splat_ordered(SceneDev sc, FrameDev fr, int *queue, float *out, int split,
-                    const float *__restrict__ absorb, float *ord_scratch) {
+                    const float *__restrict__ absorb, float *ord_scratch, int map_out) {
     if (fr.status[kStatOverflow]) return;
     extern __shared__ __align__(16) unsigned char s_raw[];
     OWarpSmem *ws = reinterpret_cast<OWarpSmem *>(s_raw) + (threadIdx.x >> 5);
@@ -277,9 +277,11 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
             }
         }
 
-        // epilogue: a whole tile writes I = beta (black background); a slice of a split
-        // tile stores its map, and the last slice composes the tile far to near
-        float *o = out + (int64_t)v * H * W * 3;
+        // epilogue: a whole tile writes I = beta (black background), or with map_out the
+        // map (alpha rgb, beta rgb); a slice of a split tile stores its map, and the last
+        // slice composes the tile far to near
+        const int oc = map_out ? 6 : 3;  // floats per pixel
+        float *o = out + (int64_t)v * H * W * oc;
         if (slot < 0) {
 #pragma unroll
             for (int r = 0; r < kONR; ++r) {
@@ -287,7 +289,13 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
 #pragma unroll
                 for (int c = 0; c < kONC; ++c) {
                     if (c * 8 + lc >= tw) continue;
-                    float *p = o + ((int64_t)(py0 + r * 4 + lr) * W + px0 + c * 8 + lc) * 3;
+                    float *p = o + ((int64_t)(py0 + r * 4 + lr) * W + px0 + c * 8 + lc) * oc;
+                    if (map_out) {
+                        p[0] = OSTATE(al, r, c, 0);
+                        p[1] = OSTATE(al, r, c, 1);
+                        p[2] = OSTATE(al, r, c, 2);
+                        p += 3;
+                    }
                     p[0] = OSTATE(be, r, c, 0);
                     p[1] = OSTATE(be, r, c, 1);
                     p[2] = OSTATE(be, r, c, 2);
@@ -318,17 +326,25 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
                 __threadfence();
                 const int TW = min(T, W - tx * T), TH = min(T, H - ty * T);
                 const int s0 = fr.item_off[gt], s1 = fr.item_off[gt + 1];
-                float *ot = o + ((int64_t)ty * T * W + (int64_t)tx * T) * 3;
+                float *ot = o + ((int64_t)ty * T * W + (int64_t)tx * T) * oc;
                 for (int k = lane; k < TH * TW * 3; k += 32) {
                     const int pix3 = k / 3, ch = k - pix3 * 3;
                     const int rr = pix3 / TW, col = pix3 - rr * TW;
                     const int pix = rr * T + col;
-                    float I = 0.0f;
+                    float A = 1.0f, I = 0.0f;
                     for (int sl = s0; sl < s1; ++sl) {
                         const float *ms = ord_scratch + (int64_t)sl * 6 * T * T;
-                        I = fmaf(__ldcg(&ms[ch * T * T + pix]), I, __ldcg(&ms[(3 + ch) * T * T + pix]));
+                        const float a = __ldcg(&ms[ch * T * T + pix]);
+                        I = fmaf(a, I, __ldcg(&ms[(3 + ch) * T * T + pix]));
+                        A *= a;
                     }
-                    ot[(int64_t)rr * W * 3 + col * 3 + ch] = I;
+                    float *q = ot + (int64_t)rr * W * oc + col * oc;
+                    if (map_out) {
+                        q[ch] = A;
+                        q[3 + ch] = I;
+                    } else {
+                        q[ch] = I;
+                    }
                 }
                 if (lane == 0) fr.tickets[slot] = 0;
             }
@@ -367,11 +383,11 @@ int ordered_ctas_per_sm() {
 int ordered_workers_per_sm() { return ordered_ctas_per_sm() * kOWarps; }
 
 cudaError_t launch_splat_ordered(const SceneDev &sc, const FrameDev &fr, int *queue, float *out,
-                                 const float *absorb, float *ord_scratch, int grid, cudaStream_t st) {
+                                 const float *absorb, float *ord_scratch, int map_out, int grid, cudaStream_t st) {
     cudaError_t err = ensure_smem_limit((const void *)k_splat_ordered, ordered_smem());
     if (err != cudaSuccess) return err;
     k_splat_ordered<<<grid, kOWarps * 32, ordered_smem(), st>>>(sc, fr, queue, out, ordered_split(fr.T), absorb,
-                                                                ord_scratch);
+                                                                ord_scratch, map_out);
     return cudaGetLastError();
 }
 

@@ -556,11 +556,13 @@ static void cross3(const double *a, const double *b, double *o) {
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-static splotch_status compose_camera(const splotch_camera *c, float m[12], float p[4]) {
+static splotch_status compose_camera(const splotch_camera *c, float m[12], float p[5]) {
     if (!c) return fail(SPLOTCH_ERR_INVALID_ARG, "camera is NULL");
     if (c->width < 1 || c->height < 1) return fail(SPLOTCH_ERR_INVALID_ARG, "image size < 1");
     if (!(c->fov_deg > 0.0 && c->fov_deg < 180.0)) return fail(SPLOTCH_ERR_INVALID_ARG, "fov outside (0, 180)");
     if (!(c->z_near > 0.0)) return fail(SPLOTCH_ERR_INVALID_ARG, "z_near <= 0");
+    const bool has_far = c->z_far > 0.0 && std::isfinite(c->z_far);
+    if (has_far && !(c->z_far > c->z_near)) return fail(SPLOTCH_ERR_INVALID_ARG, "z_far <= z_near");
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(c->eye[k]) || !std::isfinite(c->lookat[k]) || !std::isfinite(c->up[k]))
             return fail(SPLOTCH_ERR_INVALID_ARG, "camera not finite");
@@ -586,10 +588,11 @@ static splotch_status compose_camera(const splotch_camera *c, float m[12], float
     p[1] = 0.5f * (float)c->width;
     p[2] = 0.5f * (float)c->height;
     p[3] = (float)c->z_near;
+    p[4] = has_far ? (float)c->z_far : INFINITY;
     return SPLOTCH_OK;
 }
 
-extern "C" splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], float p[4]) {
+extern "C" splotch_status splotch_camera_params(const splotch_camera *cam, float m[12], float p[5]) {
     if (!m || !p) return fail(SPLOTCH_ERR_INVALID_ARG, "output is NULL");
     return compose_camera(cam, m, p);
 }
@@ -630,7 +633,7 @@ static splotch_status choose_tile(int W, int H, int requested, int *T) {
 }
 
 static splotch_status make_view(const splotch_camera *c, const splotch_render_params &pr, int T, ViewParams &v) {
-    float m[12], p[4];
+    float m[12], p[5];
     splotch_status s = compose_camera(c, m, p);
     if (s != SPLOTCH_OK) return s;
     memcpy(v.m, m, sizeof(m));
@@ -638,6 +641,7 @@ static splotch_status make_view(const splotch_camera *c, const splotch_render_pa
     v.cx = p[1];
     v.cy = p[2];
     v.zn = p[3];
+    v.zf = p[4];
     v.rfac = pr.rfac;
     v.rmin = pr.r_min_px;
     v.kexp = -kLog2e / (pr.sigma_over_R * pr.sigma_over_R);
@@ -1697,7 +1701,7 @@ extern "C" splotch_status splotch_render_ordered(splotch_scene *sc, const splotc
                                                                 (squares + 3) / 4));
     if (e == cudaSuccess)
         e = launch_splat_ordered(sc->dev_view, fr, (int *)(fixed + fh.o_queue), out, (const float *)(ex + o_abs),
-                                 (float *)(ex + o_map), grid, st);
+                                 (float *)(ex + o_map), (rs.pr.flags & SPLOTCH_OUT_MAP) ? 1 : 0, grid, st);
     int stat[4] = {0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(stat, fixed + fh.o_status, sizeof(stat), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -31,6 +31,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 struct ViewParams {
     float m[12];          // 3x4 view matrix (rows s, u, f with translations)
     float F, cx, cy, zn;  // focal length (px), image centre, near plane
+    float zf;             // far plane (+infinity when there is none)
     float rfac, rmin;     // support factor and floor
     float kexp;           // -log2(e) / sigma_over_R^2: w = exp2(d2 * kexp / R^2)
     float hd;             // 0.70710677 * T, rounded once
@@ -164,7 +165,7 @@ __device__ __forceinline__ bool raster_one(const ViewParams &v, float x, float y
     const float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(v.m[8], x), __fmul_rn(v.m[9], y)),
                                          __fmul_rn(v.m[10], z)), v.m[11]);
     o.zc = zc;
-    if (!(zc > v.zn)) return false;
+    if (!(zc > v.zn) || !(zc <= v.zf)) return false;
     const float X = __fadd_rn(v.cx, __fdiv_rn(__fmul_rn(v.F, xc), zc));
     const float Y = __fsub_rn(v.cy, __fdiv_rn(__fmul_rn(v.F, yc), zc));
     const float r = __fdiv_rn(__fmul_rn(v.F, h), zc);
@@ -337,7 +338,7 @@ int ordered_split(int T);
 int ordered_ctas_per_sm();
 int ordered_workers_per_sm();
 cudaError_t launch_splat_ordered(const SceneDev &sc, const FrameDev &fr, int *queue, float *out,
-                                 const float *absorb, float *ord_scratch, int grid, cudaStream_t st);
+                                 const float *absorb, float *ord_scratch, int map_out, int grid, cudaStream_t st);
 size_t splat_smem_bytes(int T);
 cudaError_t launch_selftest_wait(long long limit, int *result, cudaStream_t st);
 cudaError_t launch_final(float *a, int64_t count, cudaStream_t st);

@@ -22,7 +22,8 @@ class RenderParams:
     """Tile edge (0 = library default), support factor, sigma / support, minimum
     support in pixels; ``accum`` returns the accumulation a instead of 1 - exp(-a);
     ``add`` adds the accumulation to what the output holds; ``sync`` waits for the frame
-    and reports device-side timeouts."""
+    and reports device-side timeouts; ``map`` makes the depth-ordered render write the
+    per-pixel affine map (alpha, beta) instead of I."""
     tile: int = 0
     rfac: float = 0.75
     sigma_over_R: float = 0.5
@@ -33,6 +34,7 @@ class RenderParams:
     sync: bool = False
     graph: bool = False
     timing: bool = False
+    map: bool = False
 
     def c(self) -> _lib.RenderParamsC:
         p = _lib.RenderParamsC()
@@ -43,7 +45,7 @@ class RenderParams:
         p.block_particles = int(self.block_particles)
         p.flags = ((_lib.OUT_ACCUM if self.accum else 0) | (_lib.SYNC if self.sync else 0)
                    | (_lib.PLAN_GRAPH if self.graph else 0) | (_lib.TIMING if self.timing else 0)
-                   | (_lib.OUT_ADD if self.add else 0))
+                   | (_lib.OUT_ADD if self.add else 0) | (_lib.OUT_MAP if self.map else 0))
         return p
 
 
@@ -71,10 +73,10 @@ def _cams_array(cams) -> "C.Array":
 
 
 def camera_params(cam):
-    """The FP32 view matrix and {F, W/2, H/2, z_near} the kernels use."""
+    """The FP32 view matrix and {F, W/2, H/2, z_near, z_far} the kernels use."""
     lib = _lib.load()
     m = np.zeros(12, np.float32)
-    p = np.zeros(4, np.float32)
+    p = np.zeros(5, np.float32)
     c = _lib.camera_c(cam)
     check(lib.splotch_camera_params(C.byref(c), m.ctypes.data, p.ctypes.data), "camera_params")
     return m, p
@@ -230,11 +232,13 @@ class Scene:
     def render_ordered(self, cam, absorb, params: Optional[RenderParams] = None, out: Optional[torch.Tensor] = None,
                        stream=None) -> torch.Tensor:
         """Depth-ordered radiative transfer with absorption = absorb[t] x emission for
-        species t, farthest particle first (splotch_render_ordered).  Returns H x W x 3."""
+        species t, farthest particle first (splotch_render_ordered).  Returns H x W x 3, or
+        with ``params.map`` H x W x 6: the affine map (alpha rgb, beta rgb) per pixel."""
         H, W = int(cam.height), int(cam.width)
+        nc = 6 if (params is not None and params.map) else 3
         if out is None:
-            out = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
-        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == H * W * 3
+            out = torch.empty((H, W, nc), dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == H * W * nc
         ab = np.ascontiguousarray(np.broadcast_to(np.asarray(absorb, np.float32), (self.n_types,)))
         p = (params or RenderParams()).c()
         c = _lib.camera_c(cam)

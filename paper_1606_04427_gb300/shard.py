@@ -7,6 +7,13 @@ ranks sum the images, and the final transform 1 - exp(-a) runs once on the sum.
 This follows the paper's MPI model in which every task renders its particles
 independently (Section 4.2.2).  The exchange is one sum-reduce of a W x H x 3 FP32
 image per frame.
+
+With absorption different from emission the transfer (Section 2.1) depends on the
+order along each line of sight, so the frame splits by depth instead: rank k renders
+the particles of depth slab k (a camera with near / far planes at consecutive bounds,
+so each particle falls in exactly one slab) as the affine map I_out = alpha I_in + beta
+it applies to every pixel, and the maps compose far to near.  The exchange is an
+all-gather of a W x H x 6 FP32 map per rank and an ordered (non-commutative) reduction.
 """
 from __future__ import annotations
 
@@ -68,3 +75,66 @@ def render_sharded(scene_local, cam, params=None, group=None):
     reduce_accumulation(a, group)
     final_transform_(a)
     return a
+
+
+def slab_bounds(z_near: float, z_lo: float, z_hi: float, world: int) -> List[float]:
+    """world + 1 ascending depth bounds: z_near, world - 1 cuts spread evenly over
+    [z_lo, z_hi] (the depth extent the caller expects; it only balances the work), and 0
+    (no far plane).  Slab k holds the particles with bounds[k] < z_c <= bounds[k + 1]."""
+    if world < 1:
+        raise ValueError("world < 1")
+    cuts = [z_lo + (z_hi - z_lo) * k / world for k in range(1, world)]
+    cuts = [max(c, z_near * (1.0 + 1e-6) + 1e-12 * k) for k, c in enumerate(cuts, 1)]
+    for a, b in zip(cuts, cuts[1:]):
+        if not b > a:
+            raise ValueError("slab bounds must increase")
+    return [float(z_near)] + [float(c) for c in cuts] + [0.0]
+
+
+def slab_camera(cam, bounds: Sequence[float], k: int):
+    """The camera of slab k: near plane bounds[k], far plane bounds[k + 1] (0: none)."""
+    import dataclasses
+    return dataclasses.replace(cam, z_near=float(bounds[k]), z_far=float(bounds[k + 1]))
+
+
+def compose_maps(maps):
+    """Compose per-slab affine maps given far to near (maps[0] the farthest slab), each
+    an H x W x 6 array or tensor (alpha rgb, beta rgb): returns the map of all of them;
+    its beta is the frame from a black background."""
+    it = iter(maps)
+    try:
+        first = next(it)
+    except StopIteration:
+        raise ValueError("no maps") from None
+    alpha, beta = first[..., :3] * 1, first[..., 3:] * 1  # copies
+    for m in it:
+        a, b = m[..., :3], m[..., 3:]
+        beta = a * beta + b
+        alpha = a * alpha
+    if isinstance(alpha, np.ndarray):
+        return np.concatenate([alpha, beta], -1)
+    import torch
+    return torch.cat([alpha, beta], -1)
+
+
+def gather_compose(my_map, rank: int, world: int, group=None):
+    """All-gather every rank's slab map (rank k holds slab k, nearest first) and compose
+    them far to near; every rank gets the frame's H x W x 3 intensity."""
+    import torch
+    import torch.distributed as dist
+    maps = [torch.empty_like(my_map) for _ in range(world)]
+    dist.all_gather(maps, my_map.contiguous(), group=group)
+    return compose_maps(list(reversed(maps)))[..., 3:].contiguous()
+
+
+def render_ordered_sharded(scene, cam, absorb, bounds: Sequence[float], rank: int, world: int, params=None,
+                           group=None):
+    """Depth-sharded ordered frame: this rank renders slab `rank` of `bounds` as a map on
+    its GPU, and the maps of all ranks compose far to near (see gather_compose)."""
+    import dataclasses
+    from .render import RenderParams
+    if len(bounds) != world + 1:
+        raise ValueError("need world + 1 bounds")
+    pr = dataclasses.replace(params or RenderParams(), map=True)
+    mine = scene.render_ordered(slab_camera(cam, bounds, rank), absorb, pr)
+    return gather_compose(mine, rank, world, group)

@@ -46,7 +46,7 @@ def test_status_strings_and_defaults(lib):
 
 def _lib_camera(lib, cam):
     m = np.zeros(12, np.float32)
-    p = np.zeros(4, np.float32)
+    p = np.zeros(5, np.float32)
     c = _lib.camera_c(cam)
     st = lib.splotch_camera_params(C.byref(c), m.ctypes.data, p.ctypes.data)
     return st, m, p
@@ -59,6 +59,8 @@ def test_camera_composition_matches_oracle_bitwise(lib):
     cams = [synth.front_camera(256, 256), synth.front_camera(320, 200, 1.3, 60.0)]
     cams += synth.orbit_cameras(16, 1024, 1024)
     cams += [synth.random_camera(rng) for _ in range(200)]
+    for k, cam in enumerate(cams[-50:]):  # some with a far plane
+        cam.z_far = float(cam.z_near) * (2.0 + k)
     for cam in cams:
         st, m, p = _lib_camera(lib, cam)
         assert st == 0
@@ -71,7 +73,7 @@ def test_camera_composition_matches_oracle_bitwise(lib):
     dict(eye=(0.5, 3.0, 0.5)),             # up parallel to the view direction
     dict(fov_deg=0.0), dict(fov_deg=180.0), dict(fov_deg=float("nan")),
     dict(eye=(0.5, 0.5, 0.5)),             # eye == lookat
-    dict(z_near=0.0), dict(z_near=-1.0),
+    dict(z_near=0.0), dict(z_near=-1.0), dict(z_far=1e-3), dict(z_far=5e-4),
     dict(width=0), dict(height=-3),
 ])
 def test_camera_rejections_agree(lib, bad):

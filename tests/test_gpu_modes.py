@@ -335,3 +335,18 @@ def test_plan_per_view_colormaps_with_cta_tiles():
         assert np.abs(out[v].cpu().numpy() - oracle.final(oracle.render(pv, cam))).max() <= 1e-4, v
     plan.close()
     sc.close()
+
+
+@pytest.mark.parametrize("tile", [16, 40])
+def test_far_plane_matches_the_oracle(tile):
+    """A camera with a far plane culls the particles beyond it in the additive path (warp
+    and CTA kernels), as the oracle's FP32 rule does."""
+    import oracle
+    ps = synth.two_species_set(30000, 10000, 23, grid=32).with_brightness([0.05, 0.3])
+    cam = synth.front_camera(130, 100)
+    cam.z_far = 2.1
+    ref = oracle.final(oracle.render(ps, cam))
+    got = render.Scene(ps, "f32").render(cam, render.RenderParams(tile=tile)).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-4
+    full = oracle.final(oracle.render(ps, synth.front_camera(130, 100)))
+    assert np.abs(full - ref).max() > 1e-2  # the plane cut something

@@ -216,6 +216,47 @@ def test_ordered_one_crowded_tile_many_slices():
         assert np.abs(got - ref).max() <= TOL_O["f32"], tile
 
 
+@pytest.mark.parametrize("tile", [16, 32])
+def test_ordered_map_output_matches_the_oracle_map(tile):
+    """SPLOTCH_OUT_MAP: per pixel the affine map (alpha, beta) of the ordered transfer,
+    against the oracle's, on a scene with split tiles (their slices' alphas multiply)."""
+    import oracle_pins as P
+    rng = np.random.default_rng(12)
+    n = 30000
+    cm = np.array([[0.2, 0.5, 0.9], [0.9, 0.4, 0.1]], np.float32)
+    x = np.concatenate([0.5 + 0.004 * rng.standard_normal(n // 2), rng.uniform(0.3, 0.7, n - n // 2)])
+    y = np.concatenate([0.5 + 0.004 * rng.standard_normal(n // 2), rng.uniform(0.3, 0.7, n - n // 2)])
+    ps = P.make_set(x, y, rng.uniform(0.3, 0.7, n), np.exp(rng.uniform(np.log(0.002), np.log(0.02), n)),
+                    rng.uniform(0, 1, n), type_begin=[0, n // 3, n], cmaps=[cm, cm[::-1].copy()], betas=[0.03, 0.1])
+    cam = synth.front_camera(110, 90)
+    absorb = [3.0, 0.5]
+    A, B = oracle.render_rt_depth_map(ps, cam, absorb)
+    sc = render.Scene(ps, "f32")
+    assert sc.debug_bins(cam, render.RenderParams(tile=tile))[0].max() > 4096  # split tiles
+    got = sc.render_ordered(cam, absorb, render.RenderParams(tile=tile, map=True)).cpu().numpy()
+    assert got.shape == (90, 110, 6)
+    assert np.abs(got[..., :3] - A).max() <= 1e-4 and np.abs(got[..., 3:] - B).max() <= 1e-4
+    assert A.min() < 0.5  # the maps really absorb
+
+
+def test_depth_slab_maps_compose_on_the_gpu():
+    """Three depth slabs (cameras with near / far planes) rendered as maps on the GPU and
+    composed far to near equal the whole ordered frame."""
+    from paper_1606_04427_gb300 import shard
+    ps = _species_set(61)
+    cam = synth.front_camera(160, 120)
+    absorb = [2.0, 0.3]
+    sc = render.Scene(ps, "f32")
+    whole = sc.render_ordered(cam, absorb, render.RenderParams(tile=16))
+    bounds = shard.slab_bounds(cam.z_near, 1.7, 2.3, 3)
+    maps = [sc.render_ordered(shard.slab_camera(cam, bounds, k), absorb, render.RenderParams(tile=16, map=True))
+            for k in range(3)]
+    got = shard.compose_maps(list(reversed(maps)))[..., 3:]
+    assert torch.abs(got - whole).max().item() <= 2e-5
+    ref = oracle.render_rt_depth(ps, cam, absorb)
+    assert np.abs(got.cpu().numpy() - ref).max() <= TOL_O["f32"]
+
+
 def test_ordered_rejects_large_tiles_and_bad_absorption():
     sc = render.Scene(_species_set(30, 2000, 500), "f32")
     cam = synth.front_camera(128, 128)

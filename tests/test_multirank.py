@@ -40,6 +40,21 @@ def _sharded_frame(rank, world, port, out_dir):
     dist.destroy_process_group()
 
 
+def _slab_frame(rank, world, port, out_dir):
+    """Depth slabs: rank k's slab map (here from the oracle), gathered and composed far
+    to near on every rank."""
+    _init(rank, world, port)
+    import oracle
+    ps = synth.two_species_set(3000, 1000, 6, grid=32).with_brightness([0.05, 0.3])
+    cam = synth.front_camera(48, 40)
+    bounds = shard.slab_bounds(cam.z_near, 1.7, 2.3, world)
+    A, B = oracle.render_rt_depth_map(ps, shard.slab_camera(cam, bounds, rank), [2.0, 0.3])
+    mine = torch.from_numpy(np.concatenate([A, B], -1))
+    I = shard.gather_compose(mine, rank, world)
+    np.save(os.path.join(out_dir, f"s{rank}.npy"), I.numpy())
+    dist.destroy_process_group()
+
+
 def _max_timing(rank, world, port, out_dir):
     _init(rank, world, port)
     import bench
@@ -78,3 +93,28 @@ def test_bench_step_time_is_the_slowest_rank(tmp_path):
     mp.spawn(_max_timing, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
     for r in range(world):
         assert float(np.load(tmp_path / f"m{r}.npy")[0]) == 15.0
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_depth_slab_maps_compose_to_the_ordered_frame(tmp_path, world):
+    """Absorption different from emission: each rank's depth slab as an affine map, all
+    gathered and composed far to near, equals the whole depth-ordered frame."""
+    import oracle
+    mp.spawn(_slab_frame, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    ps = synth.two_species_set(3000, 1000, 6, grid=32).with_brightness([0.05, 0.3])
+    whole = oracle.render_rt_depth(ps, synth.front_camera(48, 40), [2.0, 0.3])
+    assert whole.max() > 0.1
+    for r in range(world):
+        assert np.abs(np.load(tmp_path / f"s{r}.npy") - whole).max() <= 1e-12
+
+
+def test_slab_bounds_and_composition_order():
+    b = shard.slab_bounds(1e-3, 1.5, 2.5, 4)
+    assert b[0] == 1e-3 and b[-1] == 0.0 and all(x < y for x, y in zip(b[1:-1], b[2:-1]))
+    with pytest.raises(ValueError):
+        shard.slab_bounds(1e-3, 2.0, 1.0, 3)
+    # two constant maps: far (a 0.5, b 1), near (a 0.25, b 2): I = 0.25 * 1 + 2
+    far = np.concatenate([np.full((2, 2, 3), 0.5), np.full((2, 2, 3), 1.0)], -1)
+    near = np.concatenate([np.full((2, 2, 3), 0.25), np.full((2, 2, 3), 2.0)], -1)
+    m = shard.compose_maps([far, near])
+    assert np.allclose(m[..., :3], 0.125) and np.allclose(m[..., 3:], 2.25)
