@@ -142,3 +142,45 @@ def test_render_rejects_null_and_bad_params(lib):
     assert lib.splotch_plan_destroy(None) == 0
     assert lib.splotch_destroy(None) == 0
     assert lib.splotch_workspace_bytes(None, 10, 10, 0, 10) == -1
+
+
+def test_vector_colour_without_rgb_is_rejected_before_gpu_work(lib):
+    """A species flagged vector-coloured needs the per-particle RGB field."""
+    ps = synth.plain_set(64, 0)
+    d, keep = _desc(ps, col_vector=np.array([1], np.int32))
+    h = C.c_void_p()
+    assert lib.splotch_create_scene(C.byref(d), C.byref(h)) == _lib.INVALID_ARG
+    assert b"rgb" in lib.splotch_last_error()
+    assert not h.value
+
+
+def test_entry_points_of_the_next_rows_reject_bad_arguments(lib):
+    """Argument checks that run before any GPU work: the ordered render, the out-of-core
+    render, the plan sequences and the sort hook."""
+    cam = _lib.camera_c(synth.front_camera(32, 32))
+    p = lib.splotch_default_params()
+    absorb = np.array([1.0], np.float32)
+    out = C.c_void_p(8)  # never dereferenced: the call fails first
+    assert lib.splotch_render_ordered(None, C.byref(cam), C.byref(p), absorb.ctypes.data, out, None) == _lib.INVALID_ARG
+    assert lib.splotch_plan_set_brightness(None, None, None) == _lib.INVALID_ARG
+    assert lib.splotch_plan_set_colormaps(None, None, None, None) == _lib.INVALID_ARG
+    keys = np.zeros(4, np.uint32)
+    vals = np.zeros(4, np.uint32)
+    # key width other than 4 or 8, and a bit range not a whole number of bytes
+    assert lib.splotch_debug_sort(keys.ctypes.data, 3, vals.ctypes.data, 4, 0, 8, None) == _lib.INVALID_ARG
+    assert lib.splotch_debug_sort(keys.ctypes.data, 4, vals.ctypes.data, 4, 0, 12, None) == _lib.INVALID_ARG
+    assert lib.splotch_debug_sort(keys.ctypes.data, 4, vals.ctypes.data, 4, 0, 40, None) == _lib.INVALID_ARG
+    assert lib.splotch_debug_sort(None, 8, None, -1, 0, 8, None) == _lib.INVALID_ARG
+
+
+def test_far_plane_at_or_before_the_near_plane_is_rejected(lib):
+    cam = synth.front_camera(32, 32)
+    cam.z_far = cam.z_near
+    st, _, _ = _lib_camera(lib, cam)
+    assert st == _lib.INVALID_ARG
+    cam.z_far = 3.0
+    st, _, p = _lib_camera(lib, cam)
+    assert st == 0 and p[4] == np.float32(3.0)
+    cam.z_far = 0.0
+    st, _, p = _lib_camera(lib, cam)
+    assert st == 0 and np.isinf(p[4])
