@@ -8,6 +8,11 @@ storage and FP32 accumulation.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
+Workloads: two_species_f16 (default), two_species_f32, two_species_small, clustered,
+plain, two_species_vector_f16 (stars coloured from a per-particle RGB field), batched
+(64 orbit views in one CUDA-graph plan), served (request stream), streamed (out of core
+from host memory), ordered (absorption different from emission, depth-ordered transfer).
+
 Under torchrun (N > 1) every rank renders its own replica of the frame (the
 path needs no collective for independent frames); the step time is the maximum
 over ranks and the value counts the particles of all ranks.
