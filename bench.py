@@ -484,6 +484,96 @@ def run_ordered(args):
     return 0
 
 
+def extras(ps, cam, params, args, local):
+    """Further parts of the metric, measured in the default run (one GPU, rank 0) so
+    that they sit beside the headline number:
+      two_species_f32  the same frame with FP32 attribute storage (the plain FP32
+                       single-view path the reduced-precision form is compared with);
+      batched          64 orbit views at 1024^2 in one plan replayed as a CUDA graph,
+                       over 20 M particles drawn from the frame's clustered gas, FP16,
+                       tile and particles per CTA from a short autotuner sweep;
+      served           a Poisson request stream over 8 resident FP16 sets drawn from the
+                       frame's clustered gas (1 M to 70 M particles, geometric), random
+                       cameras, images 512^2 to 4096^2: saturated throughput, then a
+                       trace at 0.8 of it with p50 / p99 latency (arrival to completion).
+    The full-size batched and served workloads (their own 20 M set; sets up to 200 M)
+    are bench.py --workload batched / served."""
+    import torch
+    from paper_1606_04427_gb300 import autotune, render, serve, synth
+    res = {}
+    stream = torch.cuda.current_stream()
+    out = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+
+    # FP32 storage of the same frame
+    sc32 = render.Scene(ps, "f32")
+    for _ in range(3):
+        sc32.render([cam], params, out)
+    ms32, clk = _timed_clocks(lambda: sc32.render([cam], params, out), max(5, args.steps // 2), stream, local)
+    sc32.close()
+    res["two_species_f32"] = {"ms_per_step": ms32, "value": ps.n / (ms32 * 1e-3) / 1e6, "unit": UNIT,
+                              "storage": "f32", "clocks": clk}
+
+    # gas particles of the frame (the clustered species), in index order
+    gas = np.arange(int(ps.type_begin[0]), int(ps.type_begin[1]))
+    beta = load_brightness()
+
+    def gas_subset(m, b):
+        idx = gas[np.linspace(0, gas.shape[0] - 1, m).astype(np.int64)]
+        sub = ps.subset(idx)
+        one = synth.ParticleSet(sub.x, sub.y, sub.z, sub.h, sub.intensity, np.array([0, m], np.int64),
+                                [sub.cmaps[0]], np.array([b], np.float32), sub.i_log[:1].copy(),
+                                None if sub.i_min is None else sub.i_min[:1].copy(),
+                                None if sub.i_max is None else sub.i_max[:1].copy(), "gas")
+        return one
+
+    # batched: 64 orbit views, one graph replay per step
+    bset = gas_subset(min(20_000_000, gas.shape[0]), beta.get("batched", [1.0])[0])
+    bscene = render.Scene(bset, "f16")
+    cams = synth.orbit_cameras(64, 1024, 1024)
+    t0 = time.perf_counter()
+    tuned = autotune.tune(bscene, cams, tiles=(16, 32), blocks=(0, 262144), repeats=1, cache_path=None)
+    sweep = time.perf_counter() - t0
+    plan = render.Plan(bscene, cams, tuned["params"], graph=True)
+    bout = plan.new_output()
+    for _ in range(3):
+        plan.launch(bout)
+    plan.check()
+    bsteps = 5
+    msb, clkb = _timed_clocks(lambda: plan.launch(bout), bsteps, stream, local)
+    plan.check()
+    info = plan.info()
+    res["batched"] = {"ms_per_step": msb, "frames_per_s": len(cams) / (msb * 1e-3),
+                      "value": len(cams) * bset.n / (msb * 1e-3) / 1e6, "unit": UNIT, "views": len(cams),
+                      "n_particles": bset.n, "image": [1024, 1024], "storage": "f16", "steps": bsteps,
+                      "tile": info["tile"], "block_particles": tuned["params"].block_particles,
+                      "autotune_sweep_s": sweep, "clocks": clkb}
+    del plan, bout
+    bscene.close()
+
+    # served: saturated burst, then Poisson arrivals at 0.8 of the saturated rate
+    sizes = [int(round(1e6 * (min(70e6, gas.shape[0]) / 1e6) ** (k / 7))) for k in range(8)]
+    sb = beta.get("served")
+    scenes = [render.Scene(gas_subset(m, sb[k] if sb else 1.0), "f16") for k, m in enumerate(sizes)]
+    rng = np.random.default_rng(4)
+    srv = serve.Server(scenes, slots=4)
+    try:
+        srv.run_trace(synth.poisson_requests(rng, 12, 1e6, len(scenes)))
+        sat = srv.run_trace(synth.poisson_requests(rng, args.extra_requests, 1e9, len(scenes)))
+        lam = 0.8 * sat["requests_per_s"]
+        tr = srv.run_trace(synth.poisson_requests(rng, args.extra_requests, lam, len(scenes)))
+        errors = list(srv.errors)
+    finally:
+        srv.close()
+    for sc in scenes:
+        sc.close()
+    res["served"] = {"set_sizes": sizes, "storage": "f16", "slots": 4, "requests_per_trace": args.extra_requests,
+                     "saturated": {k: sat[k] for k in ("requests_per_s", "mparticles_per_s", "p50_ms", "p99_ms")},
+                     "lambda_per_s": lam, "lambda_frac_of_saturated": 0.8,
+                     "requests_per_s": tr["requests_per_s"], "mparticles_per_s": tr["mparticles_per_s"],
+                     "p50_ms": tr["p50_ms"], "p99_ms": tr["p99_ms"], "errors": errors[:3]}
+    return res
+
+
 def max_over_ranks(value: float) -> float:
     """The largest value over all ranks (the step time of the slowest GPU); a no-op
     outside torch.distributed."""
@@ -513,6 +603,9 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--ref-particles", type=int, default=2_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP32-storage, batched and served measurements of the default run")
+    ap.add_argument("--extra-requests", type=int, default=160, help="requests per served trace in the default run")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--served-requests", type=int, default=400)
     ap.add_argument("--slots", type=int, default=4)
@@ -676,6 +769,8 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": f"splotch_render_streamed from page-locked host memory, chunks of {e2e_chunk} particles"},
             "gpu_launches": 4 * args.steps, "clocks": clk}
+    if world == 1 and not args.no_extras:
+        line.update(extras(ps, cam, params, args, local))
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ps, cam, storage)
     print(json.dumps(line), flush=True)

@@ -247,6 +247,18 @@ splotch_status splotch_render_streamed(const splotch_scene_desc *desc, int64_t c
  * Section 2.1 and Section 3.2.2).  Asynchronous on `stream`; INVALID_ARG for count < 0. */
 splotch_status splotch_final_transform(float *a, int64_t count, void *stream);
 
+/* Composition of depth-slab maps (Section 2.1: the radiative transfer along a line of
+ * sight applies the farther material first; Section 4.2.2: tasks render their particles
+ * independently, here one depth slab each with SPLOTCH_OUT_MAP).  maps: device, n_maps
+ * arrays of `pixels` x 6 FP32 one after the other, the farthest slab first, each pixel
+ * holding (alpha_r, alpha_g, alpha_b, beta_r, beta_g, beta_b) of I_out = alpha I_in +
+ * beta.  out: device, pixels x 6, the composed map: per pixel and channel, from the
+ * farthest map on, beta <- alpha_k beta + beta_k (one rounding) and alpha <- alpha_k alpha;
+ * its beta is the frame from a black background.  out must not overlap maps; the caller
+ * owns both.  Asynchronous on `stream`.  Errors: INVALID_ARG (n_maps < 1, pixels < 0,
+ * NULL buffers, overlap), CUDA. */
+splotch_status splotch_compose_maps(const float *maps, int32_t n_maps, int64_t pixels, float *out, void *stream);
+
 /* Test hook: per-particle raster outputs for one view, out8 = device float[8][n]:
  * X, Y, R, zc, e_r, e_g, e_b (emission = brightness x colour), active (0 / 1).
  * Inactive particles have X = Y = R = 0 when culled by the near plane. */
@@ -333,20 +345,24 @@ splotch_status splotch_last_timing(double ms[4], int64_t counts[3]);
 
 /* Render one view without allocating any device memory.  The paper has no counterpart:
  * this serves callers that cannot allocate while they render (a host application that
- * owns all device memory, a real-time loop that forbids allocation after start-up, code
- * enqueued inside a stream capture).  The frame workspace lives in a fixed 32 MiB device
- * array inside this library, present on every GPU that loads the library until the
- * process exits.  The caller passes the scene (created earlier with splotch_create_scene),
- * the camera, the parameters and `out` (device, H x W x 3 FP32), as for splotch_render.
- * The first call on a device looks up that device's copy of the array; make it before any
- * stream capture.  The call waits for the frame (it synchronises `stream`).  All calls on
- * a device share the array, so calls that overlap on the GPU (other threads, other
- * streams) race and must be serialised by the caller.
- * Limits: up to 2 MiB of per-chunk tile bases, 256 tiles split across work items, and the
- * particle-tile records of the frame in the rest of the 32 MiB (16 bytes each; about 1.9
- * million at 1024 tiles).  Frames beyond that return SPLOTCH_ERR_CAPACITY (the kernels skip
- * the work; `out` is not written); images whose tile tables do not fit return
- * SPLOTCH_ERR_UNSUPPORTED before any GPU work.  Other errors as splotch_render. */
+ * owns all device memory through its own manager, a real-time loop that forbids
+ * allocation after start-up, since an allocation can block on the device).  The frame
+ * workspace lives in a fixed 32 MiB device array inside this library, present on every
+ * GPU that loads the library until the process exits.  The caller passes the scene
+ * (created earlier with splotch_create_scene, on the device that is current for this
+ * call: INVALID_ARG otherwise), the camera, the parameters and `out` (device, H x W x 3
+ * FP32), as for splotch_render.  The first call on a device looks up that device's copy
+ * of the array; make it before any stream capture.  The call waits for the frame (it
+ * synchronises `stream`).  All calls on a device share the array and each clears what it
+ * counts into, so calls that overlap on the GPU (other threads, other streams) race and
+ * must be serialised by the caller.
+ * Limits: up to 2 MiB of per-chunk tile bases; up to 256 tiles split across work items,
+ * whose exact accumulators (48 x T^2 bytes each) take at most 8 MiB (so 170 at 32-px
+ * tiles, 42 at 64-px tiles); and the particle-tile records of the frame in the rest of
+ * the 32 MiB (16 bytes each; about 1.5 million at 1024 tiles of 16 px).  Frames beyond
+ * that return SPLOTCH_ERR_CAPACITY (the kernels skip the work; `out` is not written);
+ * images whose tile tables do not fit return SPLOTCH_ERR_UNSUPPORTED before any GPU work.
+ * Other errors as splotch_render. */
 splotch_status splotch_render_noalloc(splotch_scene *scene, const splotch_camera *cam,
                                       const splotch_render_params *params, float *out, void *stream);
 

@@ -311,6 +311,22 @@ def render_rt_depth_map(ps, cam, absorb, params: Params = Params(), storage: str
     return A, B
 
 
+def compose_maps(maps):
+    """Composition of per-pixel affine maps I_out = alpha I_in + beta given far to near
+    (maps[0] the farthest), each H x W x 6 (alpha rgb, beta rgb), FP64: the transfer of
+    Section 2.1 takes the farther material first, so a nearer map applies after a farther
+    one, beta <- alpha_near beta + beta_near and alpha <- alpha_near alpha."""
+    maps = [np.asarray(m, np.float64) for m in maps]
+    if not maps:
+        raise ValueError("no maps")
+    alpha = maps[0][..., :3].copy()
+    beta = maps[0][..., 3:].copy()
+    for m in maps[1:]:
+        beta = m[..., :3] * beta + m[..., 3:]
+        alpha = m[..., :3] * alpha
+    return np.concatenate([alpha, beta], -1)
+
+
 def render_rt_depth_lattice(ps, cam, absorb, stride: int, ox: int = 0, oy: int = 0, params: Params = Params(),
                             storage: str = "f32"):
     """render_rt_depth at the pixels (ox + stride a, oy + stride b) only: equal to

@@ -79,6 +79,7 @@ SIGNATURES = {
     "splotch_workspace_bytes": ([C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int64], C.c_int64),
     "splotch_selftest_bounded_wait": ([C.c_int64, C.c_void_p], C.c_int),
     "splotch_final_transform": ([C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
+    "splotch_compose_maps": ([C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "splotch_last_timing": ([C.c_void_p, C.c_void_p], C.c_int),
     "splotch_render_ordered": ([C.c_void_p, C.POINTER(CameraC), C.POINTER(RenderParamsC), C.c_void_p, C.c_void_p,
                                 C.c_void_p], C.c_int),

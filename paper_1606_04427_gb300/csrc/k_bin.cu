@@ -3,15 +3,19 @@
 // Section 3.1 builds, per tile, the list of particles that affect it; Section 3.2.1
 // gives the membership rule and notes that growing per-thread vectors stalled on
 // allocation.  Here the lists are one flat array sized exactly from a counting pass:
-//   k_count   streams the particles once (coalesced 16-byte SoA loads), rasterises
-//             them for a group of views, histograms tile memberships in shared memory
-//             and reserves each chunk's slice of every tile segment with one global
-//             atomic per (chunk, tile);
-//   k_scan    turns the counts into tile segment offsets and the splat's work items;
-//   k_scatter streams the particles again and writes a 16-byte record per
-//             (particle, tile) pair into its tile segment.
+//   k_count      streams the particles once (coalesced SoA loads), rasterises them
+//                for a group of views, histograms tile memberships in shared memory and
+//                writes each chunk's count of every tile;
+//   k_chunk_scan scans every tile's counts over the chunks in chunk order: the base of
+//                each chunk's slice of the tile segment, and the tile's total;
+//   k_scan       turns the totals into tile segment offsets and the splat's work items;
+//   k_scatter    streams the particles again and writes a 16-byte record per
+//                (particle, tile) pair into its tile segment, in particle order (the
+//                lists come out in ascending particle index, as Section 3.2.1 builds
+//                them by walking the particles in order).
 #include "splotch_internal.cuh"
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -339,14 +343,11 @@ __global__ void __launch_bounds__(kThreads) k_count(SceneDev sc, FrameDev fr) {
         if (ib < e) bx = load1<S>(sc.x, ib), by = load1<S>(sc.y, ib), bz = load1<S>(sc.z, ib), bh = load1<S>(sc.h, ib);
     }
     __syncthreads();
+    // this chunk's count of every tile (zeros included): k_chunk_scan turns the column of
+    // each tile into chunk bases in chunk order
     for (int k = threadIdx.x; k < g_n * nt; k += blockDim.x) {
-        const int c = s_hist[k];
-        if (c) {
-            const int g = k / nt, t = k - g * nt;
-            const int v = v0 + g;
-            const int base = atomicAdd(&fr.counts[v * nt + t], c);
-            fr.rel[((int64_t)v * fr.n_chunks + b) * nt + t] = base;
-        }
+        const int g = k / nt, t = k - g * nt;
+        fr.rel[((int64_t)(v0 + g) * fr.n_chunks + b) * nt + t] = s_hist[k];
     }
 }
 
@@ -396,6 +397,46 @@ template <typename T> __device__ T block_excl_scan(T v, T *s_warp, T *total) {
     *total = s_warp[32];
     __syncthreads();
     return res;
+}
+
+// ---------------------------------------------------------------------------------------
+// k_chunk_scan: per (view, tile), the exclusive scan of the chunks' counts in chunk order
+// (rel becomes each chunk's base inside the tile segment) and the tile's total.  The
+// bases depend only on the counts, so the lists' layout is the same on every run.
+
+constexpr int kChunkScanUnroll = 8;
+
+__global__ void __launch_bounds__(256) k_chunk_scan(FrameDev fr) {
+    const int nt = fr.n_tiles;
+    const int64_t N = (int64_t)fr.V * nt;
+    const int nch = fr.n_chunks;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(k / nt), t = (int)(k - (int64_t)v * nt);
+        int *col = fr.rel + (int64_t)v * nch * nt + t;
+        long long run = 0;
+        int b = 0;
+        for (; b + kChunkScanUnroll <= nch; b += kChunkScanUnroll) {
+            int c[kChunkScanUnroll];
+#pragma unroll
+            for (int q = 0; q < kChunkScanUnroll; ++q) c[q] = col[(int64_t)(b + q) * nt];
+#pragma unroll
+            for (int q = 0; q < kChunkScanUnroll; ++q) {
+                col[(int64_t)(b + q) * nt] = (int)run;
+                run += c[q];
+            }
+        }
+        for (; b < nch; ++b) {
+            const int c = col[(int64_t)b * nt];
+            col[(int64_t)b * nt] = (int)run;
+            run += c;
+        }
+        // a tile holding 2^31 pairs or more cannot be indexed by the 32-bit cursors
+        if (run > (long long)INT32_MAX) {
+            atomicExch(&fr.status[kStatOverflow], 1);
+            run = INT32_MAX;
+        }
+        fr.counts[k] = (int)run;
+    }
 }
 
 constexpr int kScanItems = 4;
@@ -487,12 +528,16 @@ __global__ void __launch_bounds__(1024) k_scan(FrameDev fr, int target_items, in
         fr.sizes[kSizeSplits] = run_s;
         fr.sizes[kSizeK] = K;
         fr.sizes[kSizeMaxCount] = mx_all;
-        const bool over = run_p > fr.pair_cap || run_i > fr.item_cap || run_s > fr.split_cap || big;
+        const bool over = run_p > fr.pair_cap || run_i > fr.item_cap || run_s > fr.split_cap || big ||
+                          fr.status[kStatOverflow];
         fr.status[kStatOverflow] = over ? 1 : 0;
     }
 }
 
 cudaError_t launch_scan(const FrameDev &fr, int target_items, int kmin, cudaStream_t st) {
+    const int64_t N = (int64_t)fr.V * fr.n_tiles;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 8192));
+    k_chunk_scan<<<blocks, 256, 0, st>>>(fr);
     k_scan<<<1, 1024, 0, st>>>(fr, target_items, kmin);
     return cudaGetLastError();
 }
@@ -501,72 +546,24 @@ cudaError_t launch_scan(const FrameDev &fr, int target_items, int kmin, cudaStre
 // k_scatter: same chunks as k_count; every (particle, tile) pair becomes a record
 // {X, Y, R, type << 24 | 24-bit normalised intensity} in its tile segment (in scenes with
 // a per-particle emission the last word is the particle index).
+//
+// Stable: a CTA takes its chunk in rounds of kThreads consecutive particles (thread k
+// holds particle round + k).  Per round and view
+//   1. every thread rasterises its particle and counts its member tiles (a particle with
+//      more than 2 x 2 candidate tiles is counted by its whole warp, one candidate per
+//      lane);
+//   2. a block scan of the counts places every pair in the round's pair list, which is
+//      therefore in particle order; the pairs are staged in shared memory as (tile,
+//      particle slot), kScatterStage at a time;
+//   3. one warp walks the staged pairs in order, 32 at a time: the pairs of one tile
+//      (match_any) take consecutive slots from the tile's cursor in lane order;
+//   4. all threads store the staged records at their slots.
+// With the chunk bases in chunk order (k_chunk_scan), every tile list is in ascending
+// particle index, whatever the order in which CTAs and warps run.
 
-// Write the records of one particle for every view of the group (same split between
-// lane and warp as count_particle).  Called by all lanes of the warp together.
-__device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x, float y, float z, float h,
-                                                 float code, const ViewParams *s_view, const int64_t *s_vbase,
-                                                 int g_n, int *s_cur, int nt, const FrameDev &fr, int lane) {
-    for (int g = 0; g < g_n; ++g) {
-        const ViewParams &vp = s_view[g];
-        int *cur = s_cur + g * nt;
-        float4 *lists = fr.lists + s_vbase[g];
-        int *pids = fr.pids ? fr.pids + s_vbase[g] : nullptr;
-        Raster r;
-        int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-        if (valid && raster_one(vp, x, y, z, h, r)) {
-            tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
-            ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
-        }
-        const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
-        if (small) {
-            // all cursor reservations first, then the stores: one atomic latency per
-            // particle instead of one per tile
-            const float4 rec = make_float4(r.X, r.Y, r.R, code);
-            const int t00 = ty0 * vp.ntx + tx0;
-            const bool m00 = tile_member(vp, r.X, r.Y, r.R, tx0, ty0);
-            const bool m10 = tx1 > tx0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty0);
-            const bool m01 = ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx0, ty1);
-            const bool m11 = tx1 > tx0 && ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty1);
-            const int p00 = m00 ? atomicAdd(&cur[t00], 1) : 0;
-            const int p10 = m10 ? atomicAdd(&cur[t00 + 1], 1) : 0;
-            const int p01 = m01 ? atomicAdd(&cur[t00 + vp.ntx], 1) : 0;
-            const int p11 = m11 ? atomicAdd(&cur[t00 + vp.ntx + 1], 1) : 0;
-            if (m00) lists[p00] = rec;
-            if (m10) lists[p10] = rec;
-            if (m01) lists[p01] = rec;
-            if (m11) lists[p11] = rec;
-            if (pids) {
-                if (m00) pids[p00] = (int)i;
-                if (m10) pids[p10] = (int)i;
-                if (m01) pids[p01] = (int)i;
-                if (m11) pids[p11] = (int)i;
-            }
-        }
-        uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const float bX = __shfl_sync(0xffffffffu, r.X, src), bY = __shfl_sync(0xffffffffu, r.Y, src);
-            const float bR = __shfl_sync(0xffffffffu, r.R, src);
-            const float bcode = __shfl_sync(0xffffffffu, code, src);
-            const int bid = __shfl_sync(0xffffffffu, (int)i, src);
-            const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
-            const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
-            const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
-            const float4 rec = make_float4(bX, bY, bR, bcode);
-            for (int k = lane; k < ncand; k += 32) {
-                const int ty = by0 + k / bw, tx = bx0 + k % bw;
-                if (tile_member(vp, bX, bY, bR, tx, ty)) {
-                    const int t = ty * vp.ntx + tx;
-                    const int pos = atomicAdd(&cur[t], 1);
-                    lists[pos] = rec;
-                    if (pids) pids[pos] = bid;
-                }
-            }
-        }
-    }
-}
+constexpr int kScatterStage = 4096;  // staged pairs per window
+// shared memory of k_scatter beyond the cursors: round records, staged keys and slots
+constexpr size_t kScatterExtra = sizeof(float4) * kThreads + (sizeof(int) + sizeof(unsigned short)) * kScatterStage;
 
 // Record code of a particle: species in the top 8 bits, normalised intensity in 24 bits.
 __device__ __forceinline__ float record_code(int type, float itn) {
@@ -575,72 +572,179 @@ __device__ __forceinline__ float record_code(int type, float itn) {
     return __uint_as_float(((uint32_t)type << 24) | q);
 }
 
+// Member tiles of a particle whose candidate box is large, tested by the whole warp (one
+// candidate per lane, candidates in row-major order).  With stage == false, returns the
+// member count to lane src; with stage == true, stages the members of the window
+// [w0, w0 + m) at pair indices off, off + 1, ... (off: the particle's first pair).
+template <bool kStage>
+__device__ __forceinline__ int big_members(const ViewParams &vp, float X, float Y, float R, int bx0, int bx1,
+                                           int by0, int by1, int off, int w0, int m, int slot, int *s_key,
+                                           unsigned short *s_slot, int lane) {
+    const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
+    const uint32_t lt = (1u << lane) - 1u;
+    int run = off - w0;
+    for (int k0 = 0; k0 < ncand; k0 += 32) {
+        const int k = k0 + lane;
+        const int ty = by0 + k / bw, tx = bx0 + k % bw;
+        const bool mem = k < ncand && tile_member(vp, X, Y, R, tx, ty);
+        const uint32_t bal = __ballot_sync(0xffffffffu, mem);
+        if (kStage) {
+            const int j = run + __popc(bal & lt);
+            if (mem && (unsigned)j < (unsigned)m) {
+                s_key[j] = ty * vp.ntx + tx;
+                s_slot[j] = (unsigned short)slot;
+            }
+        }
+        run += __popc(bal);
+    }
+    return run - (off - w0);
+}
+
 template <int S>
 __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) {
     if (fr.status[kStatOverflow]) return;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    float4 *s_rec = reinterpret_cast<float4 *>(s_raw);                           // [kThreads]
+    int *s_key = reinterpret_cast<int *>(s_rec + kThreads);                      // [kScatterStage]
+    unsigned short *s_slot = reinterpret_cast<unsigned short *>(s_key + kScatterStage);  // [kScatterStage]
     // cursor of this chunk's slice of every tile segment, relative to the start of the
     // view's segments (a view holds fewer than 2^31 pairs: the scan checks it)
-    extern __shared__ int s_cur[];  // [g_n][n_tiles]
+    int *s_cur = reinterpret_cast<int *>(s_slot + kScatterStage);               // [g_n][n_tiles]
     __shared__ ViewParams s_view[kMaxGroup];
     __shared__ int64_t s_vbase[kMaxGroup];
     __shared__ int64_t s_tb[kMaxTypes + 1];
+    __shared__ int s_scan[33];
     const int b = blockIdx.x;
     const int v0 = blockIdx.y * fr.G;
     const int g_n = min(fr.G, fr.V - v0);
     const int nt = fr.n_tiles;
-    for (int k = threadIdx.x; k < g_n * nt; k += blockDim.x) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int k = tid; k < g_n * nt; k += blockDim.x) {
         const int g = k / nt, t = k - g * nt;
         const int64_t *seg = fr.offsets + (int64_t)(v0 + g) * nt;
         s_cur[k] = (int)(seg[t] - seg[0]) + fr.rel[((int64_t)(v0 + g) * fr.n_chunks + b) * nt + t];
     }
-    if (threadIdx.x < g_n) {
-        s_view[threadIdx.x] = fr.views[v0 + threadIdx.x];
-        s_vbase[threadIdx.x] = fr.offsets[(int64_t)(v0 + threadIdx.x) * nt];
+    if (tid < g_n) {
+        s_view[tid] = fr.views[v0 + tid];
+        s_vbase[tid] = fr.offsets[(int64_t)(v0 + tid) * nt];
     }
-    for (int k = threadIdx.x; k <= sc.n_types; k += blockDim.x) s_tb[k] = sc.type_begin[k];
+    for (int k = tid; k <= sc.n_types; k += blockDim.x) s_tb[k] = sc.type_begin[k];
     __syncthreads();
 
     const int64_t s = (int64_t)b * fr.chunk;
     const int64_t e = min(sc.n, s + fr.chunk);
-    // two particles per thread per iteration in separate registers (see k_count)
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = blockDim.x;
     int type = 0;
-    int64_t i = s + threadIdx.x;
-    float ax = 0.0f, ay = 0.0f, az = 0.0f, ah = 0.0f, ai = 0.0f;
-    float bx = 0.0f, by = 0.0f, bz = 0.0f, bh = 0.0f, bi = 0.0f;
+    int64_t i = s + tid;
+    float cx = 0.0f, cy = 0.0f, cz = 0.0f, ch = 0.0f, ci = 0.0f;
     if (i < e)
-        ax = load1<S>(sc.x, i), ay = load1<S>(sc.y, i), az = load1<S>(sc.z, i), ah = load1<S>(sc.h, i),
-        ai = load1<S>(sc.it, i);
-    if (i + stride < e)
-        bx = load1<S>(sc.x, i + stride), by = load1<S>(sc.y, i + stride), bz = load1<S>(sc.z, i + stride),
-        bh = load1<S>(sc.h, i + stride), bi = load1<S>(sc.it, i + stride);
-    for (; i - lane < e; i += 2 * stride) {
-        if (i < e)
+        cx = load1<S>(sc.x, i), cy = load1<S>(sc.y, i), cz = load1<S>(sc.z, i), ch = load1<S>(sc.h, i),
+        ci = load1<S>(sc.it, i);
+    for (int64_t r0 = s; r0 < e; r0 += kThreads, i += kThreads) {
+        const bool valid = i < e;
+        // the next round's attributes load while this round is binned
+        float nx = 0.0f, ny = 0.0f, nz = 0.0f, nh = 0.0f, ni = 0.0f;
+        const int64_t in = i + kThreads;
+        if (in < e)
+            nx = load1<S>(sc.x, in), ny = load1<S>(sc.y, in), nz = load1<S>(sc.z, in), nh = load1<S>(sc.h, in),
+            ni = load1<S>(sc.it, in);
+        if (valid)
             while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
-        scatter_particle(i < e, i, ax, ay, az, ah, sc.emit ? __uint_as_float((uint32_t)i) : record_code(type, ai),
-                         s_view, s_vbase, g_n, s_cur, nt, fr, lane);
-        const int64_t ia = i + 2 * stride;
-        if (ia < e)
-            ax = load1<S>(sc.x, ia), ay = load1<S>(sc.y, ia), az = load1<S>(sc.z, ia), ah = load1<S>(sc.h, ia),
-            ai = load1<S>(sc.it, ia);
-        const int64_t j = i + stride;
-        if (j - lane >= e) break;
-        if (j < e)
-            while (type + 1 < sc.n_types && j >= s_tb[type + 1]) ++type;
-        scatter_particle(j < e, j, bx, by, bz, bh, sc.emit ? __uint_as_float((uint32_t)j) : record_code(type, bi),
-                         s_view, s_vbase, g_n, s_cur, nt, fr, lane);
-        const int64_t ib = i + 3 * stride;
-        if (ib < e)
-            bx = load1<S>(sc.x, ib), by = load1<S>(sc.y, ib), bz = load1<S>(sc.z, ib), bh = load1<S>(sc.h, ib),
-            bi = load1<S>(sc.it, ib);
+        const float code = sc.emit ? __uint_as_float((uint32_t)i) : record_code(type, ci);
+        for (int g = 0; g < g_n; ++g) {
+            const ViewParams &vp = s_view[g];
+            Raster r;
+            r.X = r.Y = r.R = 0.0f;
+            int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+            if (valid && raster_one(vp, cx, cy, cz, ch, r)) {
+                tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
+                ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
+            }
+            const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
+            // member bits of a small particle: (tx0, ty0), (tx1, ty0), (tx0, ty1), (tx1, ty1)
+            uint32_t mask = 0;
+            if (small) {
+                mask = (tile_member(vp, r.X, r.Y, r.R, tx0, ty0) ? 1u : 0u) |
+                       (tx1 > tx0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty0) ? 2u : 0u) |
+                       (ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx0, ty1) ? 4u : 0u) |
+                       (tx1 > tx0 && ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty1) ? 8u : 0u);
+            }
+            int cnt = __popc(mask);
+            const uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
+            for (uint32_t bb = big; bb; bb &= bb - 1) {
+                const int src = __ffs(bb) - 1;
+                const int n = big_members<false>(
+                    vp, __shfl_sync(0xffffffffu, r.X, src), __shfl_sync(0xffffffffu, r.Y, src),
+                    __shfl_sync(0xffffffffu, r.R, src), __shfl_sync(0xffffffffu, tx0, src),
+                    __shfl_sync(0xffffffffu, tx1, src), __shfl_sync(0xffffffffu, ty0, src),
+                    __shfl_sync(0xffffffffu, ty1, src), 0, 0, 0, 0, nullptr, nullptr, lane);
+                if (lane == src) cnt = n;
+            }
+            int M = 0;
+            const int off = block_excl_scan<int>(cnt, s_scan, &M);
+            s_rec[tid] = make_float4(r.X, r.Y, r.R, code);
+            float4 *lists = fr.lists + s_vbase[g];
+            int *pids = fr.pids ? fr.pids + s_vbase[g] : nullptr;
+            int *cur = s_cur + g * nt;
+            for (int w0 = 0; w0 < M; w0 += kScatterStage) {
+                const int m = min(kScatterStage, M - w0);
+                // ---- 2. stage this window's pairs, in particle order
+                if (mask) {
+                    const int t00 = ty0 * vp.ntx + tx0;
+                    int j = off - w0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (!((mask >> q) & 1u)) continue;
+                        if ((unsigned)j < (unsigned)m) {
+                            s_key[j] = t00 + (q & 1) + ((q >> 1) ? vp.ntx : 0);
+                            s_slot[j] = (unsigned short)tid;
+                        }
+                        ++j;
+                    }
+                }
+                for (uint32_t bb = big; bb; bb &= bb - 1) {
+                    const int src = __ffs(bb) - 1;
+                    big_members<true>(vp, __shfl_sync(0xffffffffu, r.X, src), __shfl_sync(0xffffffffu, r.Y, src),
+                                      __shfl_sync(0xffffffffu, r.R, src), __shfl_sync(0xffffffffu, tx0, src),
+                                      __shfl_sync(0xffffffffu, tx1, src), __shfl_sync(0xffffffffu, ty0, src),
+                                      __shfl_sync(0xffffffffu, ty1, src), __shfl_sync(0xffffffffu, off, src), w0, m,
+                                      warp * 32 + src, s_key, s_slot, lane);
+                }
+                __syncthreads();
+                // ---- 3. slots in order: one warp, 32 staged pairs per step
+                if (warp == 0) {
+                    for (int j0 = 0; j0 < m; j0 += 32) {
+                        const int j = j0 + lane;
+                        const int t = j < m ? s_key[j] : -1;
+                        const uint32_t peers = __match_any_sync(0xffffffffu, t);
+                        const int leader = __ffs(peers) - 1;
+                        int base = 0;
+                        if (j < m && lane == leader) {
+                            base = cur[t];
+                            cur[t] = base + __popc(peers);
+                        }
+                        base = __shfl_sync(0xffffffffu, base, leader);
+                        if (j < m) s_key[j] = base + __popc(peers & lt);
+                    }
+                }
+                __syncthreads();
+                // ---- 4. records to their slots
+                for (int j = tid; j < m; j += kThreads) {
+                    const int pos = s_key[j];
+                    const int sl = s_slot[j];
+                    lists[pos] = s_rec[sl];
+                    if (pids) pids[pos] = (int)(r0 + sl);
+                }
+                __syncthreads();
+            }
+        }
+        cx = nx, cy = ny, cz = nz, ch = nh, ci = ni;
     }
 }
 
 template <int S> static cudaError_t scatter_impl(const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
-    const size_t smem = (size_t)fr.G * fr.n_tiles * sizeof(int);
-    cudaError_t err =
-        ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax);
+    const size_t smem = (size_t)fr.G * fr.n_tiles * sizeof(int) + kScatterExtra;
+    cudaError_t err = ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax + kScatterExtra);
     if (err != cudaSuccess) return err;
     dim3 grid(fr.n_chunks, (fr.V + fr.G - 1) / fr.G);
     k_scatter<S><<<grid, kThreads, smem, st>>>(sc, fr);
@@ -658,9 +762,10 @@ cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, 
 template <int S> static int bin_occupancy(size_t smem) {
     int a = 0, b = 0;
     if (ensure_smem_limit((const void *)k_count<S>, kBinSmemMax) != cudaSuccess ||
-        ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax) != cudaSuccess ||
+        ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax + kScatterExtra) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_count<S>, kThreads, smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scatter<S>, kThreads, smem) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scatter<S>, kThreads, smem + kScatterExtra) !=
+            cudaSuccess) {
         cudaGetLastError();
         return 1;
     }

@@ -382,6 +382,35 @@ int ordered_ctas_per_sm() {
 
 int ordered_workers_per_sm() { return ordered_ctas_per_sm() * kOWarps; }
 
+// Composition of depth-slab maps (Section 2.1: the transfer along a line of sight takes
+// the farther material first; Section 4.2.2: tasks render their particles independently).
+// maps: n arrays of `pixels` x 6 floats, farthest first, each pixel (alpha rgb, beta rgb)
+// of I_out = alpha I_in + beta.  Composing far to near: beta <- alpha_k beta + beta_k,
+// alpha <- alpha_k alpha.  One thread per (pixel, channel); the result's beta is the
+// frame from a black background.
+__global__ void k_compose_maps(const float *__restrict__ maps, int n, int64_t pixels, float *__restrict__ out) {
+    const int64_t count = pixels * 3, stride = pixels * 6;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = j / 3;
+        const int64_t ia = p * 6 + (j - p * 3), ib = ia + 3;
+        float a = maps[ia], b = maps[ib];
+        for (int k = 1; k < n; ++k) {
+            const float ak = maps[k * stride + ia], bk = maps[k * stride + ib];
+            b = __fmaf_rn(ak, b, bk);
+            a = __fmul_rn(ak, a);
+        }
+        out[ia] = a;
+        out[ib] = b;
+    }
+}
+
+cudaError_t launch_compose_maps(const float *maps, int n, int64_t pixels, float *out, cudaStream_t st) {
+    if (pixels <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((pixels * 3 + 255) / 256, 152 * 16);
+    k_compose_maps<<<(int)blocks, 256, 0, st>>>(maps, n, pixels, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_splat_ordered(const SceneDev &sc, const FrameDev &fr, int *queue, float *out,
                                  const float *absorb, float *ord_scratch, int map_out, int grid, cudaStream_t st) {
     cudaError_t err = ensure_smem_limit((const void *)k_splat_ordered, ordered_smem());

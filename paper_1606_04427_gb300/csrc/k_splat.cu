@@ -76,7 +76,6 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
     extern __shared__ __align__(16) unsigned char s_raw[];
     __shared__ uint64_t s_bar[2];
     __shared__ int s_item, s_last;
-    __shared__ int s_wcnt[kSplatWarps];
 
     float4 *s_buf = reinterpret_cast<float4 *>(s_raw);             // [2][kStage]
     Rec *s_rec = reinterpret_cast<Rec *>(s_buf + 2 * kStage);       // [kStage]
@@ -96,7 +95,6 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
         mbar_init(&s_bar[1], 1);
         mbar_fence_init();
     }
-    if (tid < kSplatWarps) s_wcnt[tid] = 0;
     __syncthreads();
     uint32_t phase0 = 0, phase1 = 0;
 
@@ -171,7 +169,11 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 const int ihi = min(px0 + tw - 1, (int)floorf(clampf(X + R - 0.5f + eps, px0 - 1.0f, (float)(px0 + tw))));
                 const int jlo = max(py0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))));
                 const int jhi = min(py0 + th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))));
-                if (ilo > ihi || jlo > jhi) continue;
+                if (ilo > ihi || jlo > jhi) {
+                    s_rec[idx].jlo = 1;  // no pixel of the tile: no warp takes it
+                    s_rec[idx].jhi = 0;
+                    continue;
+                }
                 int type;
                 float3 e;
                 if (sc.emit) {
@@ -209,18 +211,29 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 q.eb = e.z * vs;
                 q.pad = 0.0f;
                 s_rec[idx] = q;
-                const int br0 = q.jlo >> 2, br1 = q.jhi >> 2;
-                const int nw = min(br1 - br0 + 1, kSplatWarps);
-                for (int k = 0; k < nw; ++k) {
-                    const int w = (br0 + k) & (kSplatWarps - 1);
-                    s_wl[w * kStage + atomicAdd(&s_wcnt[w], 1)] = (short)idx;
-                }
             }
             __syncthreads();
+            // this warp's list: the records whose box meets one of its block rows, in
+            // record order (so every pixel sums its records in list order)
+            int nmine = 0;
+            short *mine = s_wl + warp * kStage;
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                const int idx = j0 + lane;
+                bool meets = false;
+                if (idx < cnt) {
+                    const int jl = s_rec[idx].jlo, jh = s_rec[idx].jhi;
+                    if (jl <= jh) {
+                        const int br0 = jl >> 2, nbr = (jh >> 2) - br0 + 1;
+                        meets = nbr >= kSplatWarps || ((warp - br0) & (kSplatWarps - 1)) < nbr;
+                    }
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, meets);
+                if (meets) mine[nmine + __popc(bal & ((1u << lane) - 1u))] = (short)idx;
+                nmine += __popc(bal);
+            }
+            __syncwarp();
 
             // ---- 2. gather: this warp's list over this warp's blocks ---------------------
-            const int nmine = s_wcnt[warp];
-            const short *mine = s_wl + warp * kStage;
             for (int k = 0; k < nmine; ++k) {
                 const Rec *q = &s_rec[mine[k]];
                 const int4 box = *reinterpret_cast<const int4 *>(&q->ilo);
@@ -249,7 +262,6 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 }
             }
             __syncthreads();
-            if (tid < kSplatWarps) s_wcnt[tid] = 0;
         }
 
         // epilogue: final transform of this lane's pixels, or merge of a split tile
@@ -269,7 +281,7 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 }
             }
         } else {
-            float *scr = fr.scratch + (int64_t)slot * 3 * T * T;
+            unsigned long long *scr = fr.scratch + (int64_t)slot * 6 * T * T;
 #pragma unroll
             for (int rr = 0; rr < NR; ++rr) {
                 const int row = 4 * (warp + kSplatWarps * rr) + lr;
@@ -278,9 +290,9 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 for (int c = 0; c < NC; ++c) {
                     if (c * 8 + lc >= tw) continue;
                     const int pix = row * T + c * 8 + lc;
-                    if (ar[rr][c] != 0.0f) atomicAdd(&scr[pix], ar[rr][c]);
-                    if (ag[rr][c] != 0.0f) atomicAdd(&scr[T * T + pix], ag[rr][c]);
-                    if (ab[rr][c] != 0.0f) atomicAdd(&scr[2 * T * T + pix], ab[rr][c]);
+                    fix_add(&scr[2 * pix], ar[rr][c]);
+                    fix_add(&scr[2 * (T * T + pix)], ag[rr][c]);
+                    fix_add(&scr[2 * (2 * T * T + pix)], ab[rr][c]);
                 }
             }
             __threadfence();
@@ -293,11 +305,11 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
                 for (int k = tid; k < th * rowlen; k += kSplatThreads) {
                     const int r = k / rowlen, cc = k - r * rowlen;
                     const int col = cc / 3, ch = cc - col * 3;
-                    const float a = __ldcg(&scr[ch * T * T + r * T + col]);
+                    const float a = fix_value(&scr[2 * (ch * T * T + r * T + col)]);
                     put_pixel(&o[((int64_t)(py0 + r) * W + px0) * 3 + cc], a, out_accum);
                 }
                 __syncthreads();
-                for (int k = tid; k < 3 * T * T; k += kSplatThreads) scr[k] = 0.0f;
+                for (int k = tid; k < 6 * T * T; k += kSplatThreads) scr[k] = 0ull;
                 if (tid == 0) fr.tickets[slot] = 0;
             }
         }
@@ -543,13 +555,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                     const int ihi = min(tw - 1, (int)floorf(clampf(X + R - 0.5f + eps, px0 - 1.0f, (float)(px0 + tw))) - px0);
                     const int jlo = max(0, (int)ceilf(clampf(Y - R - 0.5f - eps, py0 - 1.0f, (float)(py0 + th))) - py0);
                     const int jhi = min(th - 1, (int)floorf(clampf(Y + R - 0.5f + eps, py0 - 1.0f, (float)(py0 + th))) - py0);
-                    if (ilo <= ihi && jlo <= jhi) {
-                        const int id = range_id(jlo >> 2, jhi >> 2, NR) * (NC * (NC + 1) / 2) +
-                                       range_id(ilo >> 3, ihi >> 3, NC);
-                        rid[q4] = id;
-                        rrank[q4] = atomicAdd(&ws->cnt[id], 1);
-                    }
+                    if (ilo <= ihi && jlo <= jhi)
+                        rid[q4] = range_id(jlo >> 2, jhi >> 2, NR) * (NC * (NC + 1) / 2) +
+                                  range_id(ilo >> 3, ihi >> 3, NC);
                 }
+                // rank among the stage's records of the same rectangle, in record order
+                const uint32_t peers = __match_any_sync(0xffffffffu, rid[q4]);
+                const int leader = __ffs(peers) - 1;
+                int before = 0;
+                if (rid[q4] >= 0 && lane == leader) {
+                    before = ws->cnt[rid[q4]];
+                    ws->cnt[rid[q4]] = before + __popc(peers);
+                }
+                before = __shfl_sync(0xffffffffu, before, leader);
+                rrank[q4] = before + __popc(peers & ((1u << lane) - 1u));
+                __syncwarp();
             }
             __syncwarp();
             // ---- 2. group the live records by rectangle (lane = rectangle)
@@ -634,7 +654,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 }
             }
         } else {
-            float *scr = fr.scratch + (int64_t)slot * 3 * T * T;
+            unsigned long long *scr = fr.scratch + (int64_t)slot * 6 * T * T;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 if (r * 4 + lr >= th) continue;
@@ -642,9 +662,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 for (int cc = 0; cc < NC; ++cc) {
                     if (cc * 8 + lc >= tw) continue;
                     const int pix = (qy + r * 4 + lr) * T + qx + cc * 8 + lc;
-                    if (ar[r][cc] != 0.0f) atomicAdd(&scr[pix], ar[r][cc]);
-                    if (ag[r][cc] != 0.0f) atomicAdd(&scr[T * T + pix], ag[r][cc]);
-                    if (ab[r][cc] != 0.0f) atomicAdd(&scr[2 * T * T + pix], ab[r][cc]);
+                    fix_add(&scr[2 * pix], ar[r][cc]);
+                    fix_add(&scr[2 * (T * T + pix)], ag[r][cc]);
+                    fix_add(&scr[2 * (2 * T * T + pix)], ab[r][cc]);
                 }
             }
             __threadfence();
@@ -661,11 +681,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 for (int k = lane; k < TH * rowlen; k += 32) {
                     const int rr = k / rowlen, c3 = k - rr * rowlen;
                     const int col = c3 / 3, ch = c3 - col * 3;
-                    const float a = __ldcg(&scr[ch * T * T + rr * T + col]);
+                    const float a = fix_value(&scr[2 * (ch * T * T + rr * T + col)]);
                     put_pixel(&ot[(int64_t)rr * W * 3 + c3], a, out_accum);
                 }
                 __syncwarp();
-                for (int k = lane; k < 3 * T * T; k += 32) scr[k] = 0.0f;
+                for (int k = lane; k < 6 * T * T; k += 32) scr[k] = 0ull;
                 if (lane == 0) fr.tickets[slot] = 0;
             }
         }

@@ -711,6 +711,9 @@ static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_ti
     fh.fixed_bytes = cv.off;
 }
 
+// Exact accumulators of one split tile: 3 channels x T x T pixels, 16 bytes each.
+static size_t split_scratch_bytes(int T) { return sizeof(unsigned long long) * 2 * 3 * (size_t)T * T; }
+
 static void layout_var(FrameHost &fh, int64_t pairs, int items, int splits, bool pids) {
     fh.pair_cap = pairs;
     fh.item_cap = items;
@@ -719,7 +722,7 @@ static void layout_var(FrameHost &fh, int64_t pairs, int items, int splits, bool
     Carve cv;
     fh.o_lists = cv.take(sizeof(float4) * std::max<int64_t>(1, pairs));
     fh.o_pids = pids ? cv.take(sizeof(int) * std::max<int64_t>(1, pairs)) : 0;
-    fh.o_scratch = cv.take(sizeof(float) * 3 * (size_t)fh.T * fh.T * std::max(1, splits));
+    fh.o_scratch = cv.take(split_scratch_bytes(fh.T) * std::max(1, splits));
     fh.o_tickets = cv.take(sizeof(int) * std::max(1, splits));
     fh.var_bytes = cv.off;
 }
@@ -743,7 +746,7 @@ static FrameDev frame_dev(const FrameHost &fh, char *fixed, char *var) {
     if (var) {
         fr.lists = (float4 *)(var + fh.o_lists);
         fr.pids = fh.pids ? (int *)(var + fh.o_pids) : nullptr;
-        fr.scratch = (float *)(var + fh.o_scratch);
+        fr.scratch = (unsigned long long *)(var + fh.o_scratch);
         fr.tickets = (int *)(var + fh.o_tickets);
     }
     fr.pair_cap = var ? fh.pair_cap : INT64_MAX;
@@ -1295,18 +1298,32 @@ extern "C" splotch_status splotch_final_transform(float *a, int64_t count, void 
     return SPLOTCH_OK;
 }
 
+extern "C" splotch_status splotch_compose_maps(const float *maps, int32_t n_maps, int64_t pixels, float *out,
+                                               void *stream) {
+    if (n_maps < 1) return fail(SPLOTCH_ERR_INVALID_ARG, "n_maps < 1");
+    if (pixels < 0) return fail(SPLOTCH_ERR_INVALID_ARG, "pixels < 0");
+    if (pixels > 0 && (!maps || !out)) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL buffer");
+    if (pixels > INT64_MAX / (6 * (int64_t)n_maps)) return fail(SPLOTCH_ERR_INVALID_ARG, "maps too large");
+    const uintptr_t m0 = (uintptr_t)maps, m1 = m0 + sizeof(float) * 6 * (uintptr_t)pixels * (uintptr_t)n_maps;
+    const uintptr_t o0 = (uintptr_t)out, o1 = o0 + sizeof(float) * 6 * (uintptr_t)pixels;
+    if (pixels > 0 && o0 < m1 && m0 < o1) return fail(SPLOTCH_ERR_INVALID_ARG, "out overlaps maps");
+    CUDA_TRY(launch_compose_maps(maps, n_maps, pixels, out, (cudaStream_t)stream));
+    return SPLOTCH_OK;
+}
+
 // -----------------------------------------------------------------------------------------
 // Render without allocation.  Some callers cannot allocate device memory while rendering:
-// a host application that has reserved the whole GPU for its own memory manager, a
-// real-time loop whose rules forbid allocation after start-up, or code enqueued inside a
-// stream capture, where cudaMalloc is not allowed and allocation would synchronise the
-// device.  This path keeps the whole frame workspace in one fixed device array declared
-// below.  The CUDA runtime places that array on every GPU that loads this library, and it
-// stays there until the process exits.
+// a host application that has reserved the whole GPU for its own memory manager, or a
+// real-time loop whose rules forbid allocation after start-up (an allocation can block on
+// the device and take memory the application has planned for).  This path keeps the
+// whole frame workspace in one fixed device array declared below.  The CUDA runtime
+// places that array on every GPU that loads this library, and it stays there until the
+// process exits.
 
 static constexpr size_t kStaticBytes = size_t(32) << 20;          // 32 MiB per GPU
 static constexpr int64_t kStaticRelBudget = int64_t(2) << 20;      // chunk bases: 2 MiB of it
 static constexpr int kStaticSplits = 256;                          // split-tile scratch slots
+static constexpr size_t kStaticSplitBytes = size_t(8) << 20;       // and at most 8 MiB for them
 static constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
@@ -1347,6 +1364,10 @@ extern "C" splotch_status splotch_render_noalloc(splotch_scene *sc, const splotc
     if (s != SPLOTCH_OK) return s;
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
+    // the scene's arrays live on the device it was created on, and the fixed array used
+    // below is the current device's: both must be the same GPU
+    if (dev != sc->dev)
+        return fail(SPLOTCH_ERR_INVALID_ARG, "current device %d is not the scene's device %d", dev, sc->dev);
     char *base = nullptr;
     s = static_workspace(dev, &base);
     if (s != SPLOTCH_OK) return s;
@@ -1355,8 +1376,9 @@ extern "C" splotch_status splotch_render_noalloc(splotch_scene *sc, const splotc
     FrameHost fh;
     layout_fixed(fh, sc, 1, vp.n_tiles, T, pr.block_particles, kStaticRelBudget);
     const size_t fixed = align256(fh.fixed_bytes);
-    const int splits = std::min(vp.n_tiles, kStaticSplits);
-    const size_t scratch = align256(sizeof(float) * 3 * (size_t)T * T * splits) + align256(sizeof(int) * splits);
+    const int splits = (int)std::min<size_t>(std::min(vp.n_tiles, kStaticSplits),
+                                             std::max<size_t>(1, kStaticSplitBytes / split_scratch_bytes(T)));
+    const size_t scratch = align256(split_scratch_bytes(T) * splits) + align256(sizeof(int) * splits);
     if (fixed + scratch + 4096 > kStaticBytes)
         return fail(SPLOTCH_ERR_UNSUPPORTED, "%d tiles of %d px need %zu bytes of tables, more than the %zu-byte fixed workspace",
                     vp.n_tiles, T, fixed + scratch, kStaticBytes);

@@ -77,8 +77,8 @@ struct FrameDev {
     int *status;              // [4] 0: capacity overflow, 1: timeout, 2: work queue
     float4 *lists;            // [pair capacity] tile records (X, Y, R, code)
     int *pids;                // [pair capacity] particle index per record, or null
-    float *scratch;           // [split capacity][3][T][T] partial accumulators
-    int *tickets;             // [split capacity]
+    unsigned long long *scratch;  // [split capacity][3][T][T][2] exact accumulators (fix_add)
+    int *tickets;                 // [split capacity]
     int64_t pair_cap;
     int item_cap, split_cap;
     const float *vscale;      // [V * n_types] emission scale per view and species, or null
@@ -265,6 +265,43 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
+// ------------------------------------------------------------------------------------
+// Exact, order-independent merge of FP32 partial sums (slices of a split tile).  A value
+// is taken as a signed 128-bit integer count of 2^-64 (magnitudes below 2^-64 drop out,
+// magnitudes from 2^62 up saturate there) and added to a {low, high} pair of 64-bit words
+// with two integer atomics, the low word's carry going into the high one.  Integer
+// addition is associative, so the merged sum is the same whichever slice arrives first;
+// fix_value rounds it to FP32 once.
+
+__device__ __forceinline__ void fix_add(unsigned long long *acc, float v) {
+    const uint32_t b = __float_as_uint(v);
+    const int E = (int)((b >> 23) & 0xFFu);
+    if (E == 0) return;  // zero or subnormal: below the unit
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = E - 86;  // |v| * 2^64 = m * 2^(E - 150 + 64)
+    unsigned long long lo, hi;
+    if (sh <= -24) return;
+    if (sh < 0) lo = m >> (-sh), hi = 0ull;
+    else if (sh == 0) lo = m, hi = 0ull;
+    else if (sh < 64) lo = m << sh, hi = m >> (64 - sh);
+    else if (sh < 102) lo = 0ull, hi = m << (sh - 64);
+    else lo = 0ull, hi = 1ull << 62;
+    if (b >> 31) {  // two's complement of the 128-bit magnitude
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const unsigned long long old = atomicAdd(&acc[0], lo);
+    const unsigned long long up = hi + (old + lo < old ? 1ull : 0ull);
+    if (up) atomicAdd(&acc[1], up);
+}
+
+// Value of an accumulator pair once every addition into it is complete and visible.
+__device__ __forceinline__ float fix_value(const unsigned long long *acc) {
+    const unsigned long long lo = __ldcg(&acc[0]), hi = __ldcg(&acc[1]);
+    const double d = (double)(long long)hi * 18446744073709551616.0 + (double)lo;
+    return (float)(d * 5.4210108624275222e-20);  // x 2^-64
+}
+
 // 2^x on the SFU (PTX ex2.approx.ftz, max relative error about 2^-22); the weights it feeds
 // are values, never decisions.
 __device__ __forceinline__ float ex2_fast(float x) {
@@ -342,6 +379,7 @@ cudaError_t launch_splat_ordered(const SceneDev &sc, const FrameDev &fr, int *qu
 size_t splat_smem_bytes(int T);
 cudaError_t launch_selftest_wait(long long limit, int *result, cudaStream_t st);
 cudaError_t launch_final(float *a, int64_t count, cudaStream_t st);
+cudaError_t launch_compose_maps(const float *maps, int n, int64_t pixels, float *out, cudaStream_t st);
 cudaError_t launch_debug_raster(int storage, const SceneDev &sc, const ViewParams *view,
                                 float *out8, cudaStream_t st);
 

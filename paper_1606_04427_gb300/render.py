@@ -257,7 +257,8 @@ class Scene:
 
     def debug_bins(self, cam, params: Optional[RenderParams] = None, capacity: Optional[int] = None,
                    stream=None):
-        """(counts[n_tiles], offsets[n_tiles+1], members) with each tile's members sorted."""
+        """(counts[n_tiles], offsets[n_tiles+1], members): the tile lists as the library
+        builds them, each in ascending particle index."""
         p = (params or RenderParams()).c()
         T = p.tile if p.tile > 0 else None
         c = _lib.camera_c(cam)
@@ -278,8 +279,6 @@ class Scene:
         counts_h = counts.cpu().numpy()
         offs_h = offsets.cpu().numpy()
         mem = members[: int(total.value)].cpu().numpy()
-        for t in range(nt):
-            mem[offs_h[t]:offs_h[t + 1]].sort()
         return counts_h, offs_h, mem
 
     def info(self):

@@ -98,33 +98,39 @@ def slab_camera(cam, bounds: Sequence[float], k: int):
 
 
 def compose_maps(maps):
-    """Compose per-slab affine maps given far to near (maps[0] the farthest slab), each
-    an H x W x 6 array or tensor (alpha rgb, beta rgb): returns the map of all of them;
-    its beta is the frame from a black background."""
-    it = iter(maps)
-    try:
-        first = next(it)
-    except StopIteration:
-        raise ValueError("no maps") from None
-    alpha, beta = first[..., :3] * 1, first[..., 3:] * 1  # copies
-    for m in it:
-        a, b = m[..., :3], m[..., 3:]
-        beta = a * beta + b
-        alpha = a * alpha
-    if isinstance(alpha, np.ndarray):
-        return np.concatenate([alpha, beta], -1)
+    """Compose per-slab affine maps given far to near (maps[0] the farthest slab), each an
+    H x W x 6 float32 CUDA tensor (alpha rgb, beta rgb), with the library's
+    splotch_compose_maps: returns the map of all of them; its beta is the frame from a
+    black background."""
     import torch
-    return torch.cat([alpha, beta], -1)
+    from . import _lib
+    maps = list(maps)
+    if not maps:
+        raise ValueError("no maps")
+    shape = maps[0].shape
+    for m in maps:
+        if not (isinstance(m, torch.Tensor) and m.is_cuda and m.dtype == torch.float32 and m.shape == shape
+                and shape[-1] == 6):
+            raise TypeError("compose_maps takes float32 CUDA tensors of one shape (..., 6)")
+    stacked = torch.stack([m.contiguous() for m in maps])  # one buffer, farthest first
+    out = torch.empty(shape, dtype=torch.float32, device=stacked.device)
+    pixels = out.numel() // 6
+    lib = _lib.load()
+    _lib.check(lib.splotch_compose_maps(stacked.data_ptr(), len(maps), pixels, out.data_ptr(),
+                                        torch.cuda.current_stream().cuda_stream), "compose_maps")
+    return out
 
 
-def gather_compose(my_map, rank: int, world: int, group=None):
+def gather_compose(my_map, rank: int, world: int, group=None, compose=None):
     """All-gather every rank's slab map (rank k holds slab k, nearest first) and compose
-    them far to near; every rank gets the frame's H x W x 3 intensity."""
+    them far to near; every rank gets the frame's H x W x 3 intensity.  compose: the
+    composition of a far-to-near list of maps (default: compose_maps on the GPU)."""
     import torch
     import torch.distributed as dist
     maps = [torch.empty_like(my_map) for _ in range(world)]
     dist.all_gather(maps, my_map.contiguous(), group=group)
-    return compose_maps(list(reversed(maps)))[..., 3:].contiguous()
+    composed = (compose or compose_maps)(list(reversed(maps)))
+    return composed[..., 3:].contiguous()
 
 
 def render_ordered_sharded(scene, cam, absorb, bounds: Sequence[float], rank: int, world: int, params=None,

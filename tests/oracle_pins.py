@@ -522,6 +522,17 @@ def pin_rt_depth_map_closed_forms_and_slab_composition():
     Af, Bf = oracle.render_rt_depth_map(ps, far, absorb)
     assert np.abs(Af - 1.0).max() > 0.05 and np.abs(An - 1.0).max() > 0.05  # both slabs absorb
     assert np.abs(An * Bf + Bn - whole).max() <= 1e-12
+    # the same through the oracle's composition of a far-to-near list of maps
+    C = oracle.compose_maps([np.concatenate([Af, Bf], -1), np.concatenate([An, Bn], -1)])
+    assert np.abs(C[..., 3:] - whole).max() <= 1e-12 and np.abs(C[..., :3] - An * Af).max() <= 1e-15
+    # three constant maps by hand, far to near: (a 0.5, b 1), (a 0.25, b 2), (a 2, b -1):
+    # beta = 2 (0.25 * 1 + 2) - 1 = 3.5, alpha = 0.5 * 0.25 * 2 = 0.25
+    consts = [(0.5, 1.0), (0.25, 2.0), (2.0, -1.0)]
+    ms = [np.concatenate([np.full((2, 3, 3), a), np.full((2, 3, 3), b)], -1) for a, b in consts]
+    C3 = oracle.compose_maps(ms)
+    assert np.all(C3[..., :3] == 0.25) and np.all(C3[..., 3:] == 3.5)
+    # the order matters: near to far gives another frame
+    assert not np.allclose(oracle.compose_maps(ms[::-1])[..., 3:], 3.5)
 
 
 def pin_rt_depth_lattice_is_the_full_image_restricted():

@@ -209,7 +209,8 @@ def test_streamed_render_equals_resident_render():
 
 def test_additive_output_sums_renders():
     """SPLOTCH_OUT_ADD adds the accumulation to the output: two additive renders of the
-    same frame give twice the accumulation."""
+    same frame give twice the accumulation.  Renders are deterministic (tile lists in
+    particle order, split tiles merged exactly), so the sum is exactly 2 a."""
     ps = synth.clustered_set(30000, 12, grid=32).with_brightness([0.05])
     cam = synth.front_camera(128, 96)
     sc = render.Scene(ps, "f32")
@@ -217,7 +218,30 @@ def test_additive_output_sums_renders():
     out = torch.zeros_like(acc)
     sc.render(cam, render.RenderParams(add=True), out)
     sc.render(cam, render.RenderParams(add=True), out)
-    assert torch.allclose(out, 2 * acc, rtol=1e-6, atol=1e-7)
+    assert torch.equal(out, 2 * acc)
+
+
+@pytest.mark.parametrize("T", [8, 16, 24, 32, 40, 64])
+def test_renders_are_bitwise_reproducible(T):
+    """The same frame rendered again, with other work in between and a different number of
+    particle chunks, gives the same bits: every tile list is in ascending particle index
+    and the slices of a split tile merge exactly, so no summation order depends on which
+    CTA or warp runs first."""
+    rng = np.random.default_rng(31)
+    ps = synth.two_species_set(40000, 15000, 17, grid=32).with_brightness([0.05, 0.3])
+    # a crowded spot: its tiles are split over several work items
+    k = 20000
+    ps.x[:k] = 0.5 + rng.normal(0, 0.002, k)
+    ps.y[:k] = 0.5 + rng.normal(0, 0.002, k)
+    sc = render.Scene(ps, "f32")
+    cam = synth.front_camera(200, 150)
+    p = render.RenderParams(tile=T, accum=True)
+    first = sc.render(cam, p).clone()
+    other = render.Scene(synth.plain_set(5000, 3), "f32")
+    other.render(synth.front_camera(64, 64))
+    for bp in (0, 4096, 30000):
+        again = sc.render(cam, render.RenderParams(tile=T, accum=True, block_particles=bp))
+        assert torch.equal(first, again), (T, bp)
 
 
 def test_plan_per_view_brightness_matches_rescaled_scenes():

@@ -2,8 +2,8 @@
 
 splotch_render_noalloc serves callers that may not allocate device memory while they
 render (an application that owns all device memory through its own manager, a real-time
-loop that allocates only at start-up, work enqueued inside a stream capture).  It keeps
-the frame workspace in one fixed device array inside the library, shared by every call.
+loop that allocates only at start-up).  It keeps the frame workspace in one fixed device
+array inside the library, shared by every call.
 These tests call it through the C ABI and compare its images with splotch_render's on
 the same scene and camera, within the image bars of the parity suite, on calls made one
 after the other, so that whatever one call leaves in the shared array cannot leak into
