@@ -153,7 +153,13 @@ typedef struct {
  *                 sequence into a CUDA graph on first launch and replays it afterwards;
  *                 SPLOTCH_TIMING: splotch_render records CUDA events around each kernel on
  *                 `stream`, waits for the frame and keeps the durations for
- *                 splotch_last_timing. */
+ *                 splotch_last_timing; SPLOTCH_STABLE: build every tile list in ascending
+ *                 particle index (Section 3.2.1 fills each thread's index vectors by walking
+ *                 its particles in order), which makes the image bitwise reproducible; the
+ *                 binning takes about three times as long.  Without it a list holds the
+ *                 same members, each chunk's in the order its warps reached them, and two
+ *                 renders may differ by the FP32 rounding of a pixel's sum in another order
+ *                 (at most 2 (n - 1) 2^-24 of the sum, n its contributions). */
 typedef struct {
     int32_t tile;
     float rfac;
@@ -165,7 +171,8 @@ typedef struct {
 
 enum {
     SPLOTCH_OUT_ACCUM = 1, SPLOTCH_SYNC = 2, SPLOTCH_PLAN_GRAPH = 4, SPLOTCH_TIMING = 8, SPLOTCH_OUT_ADD = 16,
-    SPLOTCH_OUT_MAP = 32  /* splotch_render_ordered: write the per-pixel affine map (alpha, beta) */
+    SPLOTCH_OUT_MAP = 32, /* splotch_render_ordered: write the per-pixel affine map (alpha, beta) */
+    SPLOTCH_STABLE = 64   /* tile lists in ascending particle index: bitwise reproducible images */
 };
 
 /* Defaults listed above. */

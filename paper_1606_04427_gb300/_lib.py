@@ -15,7 +15,7 @@ from . import build as _build
 OK, INVALID_ARG, OOM, CUDA, CAPACITY, TIMEOUT, UNSUPPORTED = range(7)
 F32, F16, BF16 = 0, 1, 2
 STORAGE = {"f32": F32, "f16": F16, "bf16": BF16}
-OUT_ACCUM, SYNC, PLAN_GRAPH, TIMING, OUT_ADD, OUT_MAP = 1, 2, 4, 8, 16, 32
+OUT_ACCUM, SYNC, PLAN_GRAPH, TIMING, OUT_ADD, OUT_MAP, STABLE = 1, 2, 4, 8, 16, 32, 64
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)

@@ -32,6 +32,9 @@ cudaError_t ensure_smem_limit(const void *kernel, size_t bytes) {
     size_t &cur = set[std::make_pair(kernel, dev)];
     if (cur >= bytes) return cudaSuccess;
     err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // the largest shared-memory carveout, so that the CTAs the occupancy allows all fit
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (err == cudaSuccess) cur = bytes;
     return err;
 }
@@ -545,25 +548,76 @@ cudaError_t launch_scan(const FrameDev &fr, int target_items, int kmin, cudaStre
 // ---------------------------------------------------------------------------------------
 // k_scatter: same chunks as k_count; every (particle, tile) pair becomes a record
 // {X, Y, R, type << 24 | 24-bit normalised intensity} in its tile segment (in scenes with
-// a per-particle emission the last word is the particle index).
-//
-// Stable: a CTA takes its chunk in rounds of kThreads consecutive particles (thread k
-// holds particle round + k).  Per round and view
-//   1. every thread rasterises its particle and counts its member tiles (a particle with
-//      more than 2 x 2 candidate tiles is counted by its whole warp, one candidate per
-//      lane);
-//   2. a block scan of the counts places every pair in the round's pair list, which is
-//      therefore in particle order; the pairs are staged in shared memory as (tile,
-//      particle slot), kScatterStage at a time;
-//   3. one warp walks the staged pairs in order, 32 at a time: the pairs of one tile
-//      (match_any) take consecutive slots from the tile's cursor in lane order;
-//   4. all threads store the staged records at their slots.
-// With the chunk bases in chunk order (k_chunk_scan), every tile list is in ascending
-// particle index, whatever the order in which CTAs and warps run.
+// a per-particle emission the last word is the particle index).  Each chunk fills its
+// slice of a tile segment (slices in chunk order, k_chunk_scan) through a shared-memory
+// cursor per tile: the slice holds exactly the chunk's members of the tile, in the order
+// the CTA's warps reached them.  k_scatter_stable (below) orders them by particle index.
 
-constexpr int kScatterStage = 4096;  // staged pairs per window
-// shared memory of k_scatter beyond the cursors: round records, staged keys and slots
-constexpr size_t kScatterExtra = sizeof(float4) * kThreads + (sizeof(int) + sizeof(unsigned short)) * kScatterStage;
+// Write the records of one particle for every view of the group (same split between
+// lane and warp as count_particle).  Called by all lanes of the warp together.
+__device__ __forceinline__ void scatter_particle(bool valid, int64_t i, float x, float y, float z, float h,
+                                                 float code, const ViewParams *s_view, const int64_t *s_vbase,
+                                                 int g_n, int *s_cur, int nt, const FrameDev &fr, int lane) {
+    for (int g = 0; g < g_n; ++g) {
+        const ViewParams &vp = s_view[g];
+        int *cur = s_cur + g * nt;
+        float4 *lists = fr.lists + s_vbase[g];
+        int *pids = fr.pids ? fr.pids + s_vbase[g] : nullptr;
+        Raster r;
+        int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+        if (valid && raster_one(vp, x, y, z, h, r)) {
+            tx0 = tile_of(vp, r.i0), tx1 = tile_of(vp, r.i1);
+            ty0 = tile_of(vp, r.j0), ty1 = tile_of(vp, r.j1);
+        }
+        const bool small = tx1 >= tx0 && tx1 - tx0 <= 1 && ty1 - ty0 <= 1;
+        if (small) {
+            // all cursor reservations first, then the stores: one atomic latency per
+            // particle instead of one per tile
+            const float4 rec = make_float4(r.X, r.Y, r.R, code);
+            const int t00 = ty0 * vp.ntx + tx0;
+            const bool m00 = tile_member(vp, r.X, r.Y, r.R, tx0, ty0);
+            const bool m10 = tx1 > tx0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty0);
+            const bool m01 = ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx0, ty1);
+            const bool m11 = tx1 > tx0 && ty1 > ty0 && tile_member(vp, r.X, r.Y, r.R, tx1, ty1);
+            const int p00 = m00 ? atomicAdd(&cur[t00], 1) : 0;
+            const int p10 = m10 ? atomicAdd(&cur[t00 + 1], 1) : 0;
+            const int p01 = m01 ? atomicAdd(&cur[t00 + vp.ntx], 1) : 0;
+            const int p11 = m11 ? atomicAdd(&cur[t00 + vp.ntx + 1], 1) : 0;
+            if (m00) lists[p00] = rec;
+            if (m10) lists[p10] = rec;
+            if (m01) lists[p01] = rec;
+            if (m11) lists[p11] = rec;
+            if (pids) {
+                if (m00) pids[p00] = (int)i;
+                if (m10) pids[p10] = (int)i;
+                if (m01) pids[p01] = (int)i;
+                if (m11) pids[p11] = (int)i;
+            }
+        }
+        uint32_t big = __ballot_sync(0xffffffffu, tx1 >= tx0 && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const float bX = __shfl_sync(0xffffffffu, r.X, src), bY = __shfl_sync(0xffffffffu, r.Y, src);
+            const float bR = __shfl_sync(0xffffffffu, r.R, src);
+            const float bcode = __shfl_sync(0xffffffffu, code, src);
+            const int bid = __shfl_sync(0xffffffffu, (int)i, src);
+            const int bx0 = __shfl_sync(0xffffffffu, tx0, src), bx1 = __shfl_sync(0xffffffffu, tx1, src);
+            const int by0 = __shfl_sync(0xffffffffu, ty0, src), by1 = __shfl_sync(0xffffffffu, ty1, src);
+            const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
+            const float4 rec = make_float4(bX, bY, bR, bcode);
+            for (int k = lane; k < ncand; k += 32) {
+                const int ty = by0 + k / bw, tx = bx0 + k % bw;
+                if (tile_member(vp, bX, bY, bR, tx, ty)) {
+                    const int t = ty * vp.ntx + tx;
+                    const int pos = atomicAdd(&cur[t], 1);
+                    lists[pos] = rec;
+                    if (pids) pids[pos] = bid;
+                }
+            }
+        }
+    }
+}
 
 // Record code of a particle: species in the top 8 bits, normalised intensity in 24 bits.
 __device__ __forceinline__ float record_code(int type, float itn) {
@@ -572,44 +626,150 @@ __device__ __forceinline__ float record_code(int type, float itn) {
     return __uint_as_float(((uint32_t)type << 24) | q);
 }
 
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) {
+    if (fr.status[kStatOverflow]) return;
+    // cursor of this chunk's slice of every tile segment, relative to the start of the
+    // view's segments (a view holds fewer than 2^31 pairs: the scan checks it)
+    extern __shared__ int s_cur[];  // [g_n][n_tiles]
+    __shared__ ViewParams s_view[kMaxGroup];
+    __shared__ int64_t s_vbase[kMaxGroup];
+    __shared__ int64_t s_tb[kMaxTypes + 1];
+    const int b = blockIdx.x;
+    const int v0 = blockIdx.y * fr.G;
+    const int g_n = min(fr.G, fr.V - v0);
+    const int nt = fr.n_tiles;
+    for (int k = threadIdx.x; k < g_n * nt; k += blockDim.x) {
+        const int g = k / nt, t = k - g * nt;
+        const int64_t *seg = fr.offsets + (int64_t)(v0 + g) * nt;
+        s_cur[k] = (int)(seg[t] - seg[0]) + fr.rel[((int64_t)(v0 + g) * fr.n_chunks + b) * nt + t];
+    }
+    if (threadIdx.x < g_n) {
+        s_view[threadIdx.x] = fr.views[v0 + threadIdx.x];
+        s_vbase[threadIdx.x] = fr.offsets[(int64_t)(v0 + threadIdx.x) * nt];
+    }
+    for (int k = threadIdx.x; k <= sc.n_types; k += blockDim.x) s_tb[k] = sc.type_begin[k];
+    __syncthreads();
+
+    const int64_t s = (int64_t)b * fr.chunk;
+    const int64_t e = min(sc.n, s + fr.chunk);
+    // two particles per thread per iteration in separate registers (see k_count)
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = blockDim.x;
+    int type = 0;
+    int64_t i = s + threadIdx.x;
+    float ax = 0.0f, ay = 0.0f, az = 0.0f, ah = 0.0f, ai = 0.0f;
+    float bx = 0.0f, by = 0.0f, bz = 0.0f, bh = 0.0f, bi = 0.0f;
+    if (i < e)
+        ax = load1<S>(sc.x, i), ay = load1<S>(sc.y, i), az = load1<S>(sc.z, i), ah = load1<S>(sc.h, i),
+        ai = load1<S>(sc.it, i);
+    if (i + stride < e)
+        bx = load1<S>(sc.x, i + stride), by = load1<S>(sc.y, i + stride), bz = load1<S>(sc.z, i + stride),
+        bh = load1<S>(sc.h, i + stride), bi = load1<S>(sc.it, i + stride);
+    for (; i - lane < e; i += 2 * stride) {
+        if (i < e)
+            while (type + 1 < sc.n_types && i >= s_tb[type + 1]) ++type;
+        scatter_particle(i < e, i, ax, ay, az, ah, sc.emit ? __uint_as_float((uint32_t)i) : record_code(type, ai),
+                         s_view, s_vbase, g_n, s_cur, nt, fr, lane);
+        const int64_t ia = i + 2 * stride;
+        if (ia < e)
+            ax = load1<S>(sc.x, ia), ay = load1<S>(sc.y, ia), az = load1<S>(sc.z, ia), ah = load1<S>(sc.h, ia),
+            ai = load1<S>(sc.it, ia);
+        const int64_t j = i + stride;
+        if (j - lane >= e) break;
+        if (j < e)
+            while (type + 1 < sc.n_types && j >= s_tb[type + 1]) ++type;
+        scatter_particle(j < e, j, bx, by, bz, bh, sc.emit ? __uint_as_float((uint32_t)j) : record_code(type, bi),
+                         s_view, s_vbase, g_n, s_cur, nt, fr, lane);
+        const int64_t ib = i + 3 * stride;
+        if (ib < e)
+            bx = load1<S>(sc.x, ib), by = load1<S>(sc.y, ib), bz = load1<S>(sc.z, ib), bh = load1<S>(sc.h, ib),
+            bi = load1<S>(sc.it, ib);
+    }
+}
+
+template <int S> static cudaError_t scatter_impl(const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
+    const size_t smem = (size_t)fr.G * fr.n_tiles * sizeof(int);
+    cudaError_t err =
+        ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax);
+    if (err != cudaSuccess) return err;
+    dim3 grid(fr.n_chunks, (fr.V + fr.G - 1) / fr.G);
+    k_scatter<S><<<grid, kThreads, smem, st>>>(sc, fr);
+    return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------------------
+// k_scatter_stable: the same slices, each in ascending particle index (as the per-thread
+// index vectors of Section 3.2.1 are filled by walking each thread's particle range in
+// order).  A CTA takes its chunk in rounds of kThreads consecutive particles (thread k
+// holds particle round + k).  Per round and view
+//   1. every thread rasterises its particle and counts its member tiles (a particle with
+//      more than 2 x 2 candidate tiles is counted by its whole warp, one candidate per
+//      lane);
+//   2. a block scan of the counts places every pair in the round's pair list, which is
+//      therefore in particle order; the pairs are staged in shared memory as (tile,
+//      particle slot), kStableStage at a time;
+//   3. every 32-pair slice finds, for each pair, the other pairs of its tile (the key
+//      bits compared with ballots) and its rank among them; then one warp walks the
+//      slices in order and, per tile of each slice, takes that many consecutive slots
+//      from the tile's cursor;
+//   4. all threads store the staged records at their slots (slice base + rank).
+// With the chunk bases in chunk order, every tile list is in ascending particle index
+// whatever the order in which CTAs and warps run, so images do not depend on it.  The
+// ranking costs about twice the scatter's time; renders ask for it with SPLOTCH_STABLE.
+
+constexpr int kStableStage = 2048;  // staged pairs per window
+// shared memory beyond the cursors: round records, staged keys, slots and slice ranks
+constexpr size_t kStableExtra = sizeof(float4) * kThreads + (sizeof(int) + 2 * sizeof(unsigned short)) * kStableStage;
+// key bits compared per slice: tile indices are below kMaxTiles = 2^14, and bit 14 marks
+// the lanes past the window's end
+constexpr int kTileKeyBits = 15;
+constexpr uint32_t kNoTile = 1u << 14;
+static_assert(kMaxTiles <= (int)kNoTile, "tile keys need more bits");
+
 // Member tiles of a particle whose candidate box is large, tested by the whole warp (one
-// candidate per lane, candidates in row-major order).  With stage == false, returns the
-// member count to lane src; with stage == true, stages the members of the window
-// [w0, w0 + m) at pair indices off, off + 1, ... (off: the particle's first pair).
+// candidate per lane, candidates in row-major order).  With kStage false, returns the
+// member count; with kStage true, stages the members of the window [w0, w0 + m) at pair
+// indices off, off + 1, ... (off: the particle's first pair).
 template <bool kStage>
 __device__ __forceinline__ int big_members(const ViewParams &vp, float X, float Y, float R, int bx0, int bx1,
                                            int by0, int by1, int off, int w0, int m, int slot, int *s_key,
                                            unsigned short *s_slot, int lane) {
-    const int bw = bx1 - bx0 + 1, ncand = bw * (by1 - by0 + 1);
+    const int bw = bx1 - bx0 + 1, bh = by1 - by0 + 1;
     const uint32_t lt = (1u << lane) - 1u;
     int run = off - w0;
-    for (int k0 = 0; k0 < ncand; k0 += 32) {
-        const int k = k0 + lane;
-        const int ty = by0 + k / bw, tx = bx0 + k % bw;
-        const bool mem = k < ncand && tile_member(vp, X, Y, R, tx, ty);
-        const uint32_t bal = __ballot_sync(0xffffffffu, mem);
-        if (kStage) {
-            const int j = run + __popc(bal & lt);
-            if (mem && (unsigned)j < (unsigned)m) {
-                s_key[j] = ty * vp.ntx + tx;
-                s_slot[j] = (unsigned short)slot;
+    for (int dy = 0; dy < bh; ++dy) {
+        for (int dx0 = 0; dx0 < bw; dx0 += 32) {
+            const int tx = bx0 + dx0 + lane, ty = by0 + dy;
+            const bool mem = dx0 + lane < bw && tile_member(vp, X, Y, R, tx, ty);
+            const uint32_t bal = __ballot_sync(0xffffffffu, mem);
+            if (kStage) {
+                const int j = run + __popc(bal & lt);
+                if (mem && (unsigned)j < (unsigned)m) {
+                    s_key[j] = ty * vp.ntx + tx;
+                    s_slot[j] = (unsigned short)slot;
+                }
             }
+            run += __popc(bal);
         }
-        run += __popc(bal);
     }
     return run - (off - w0);
 }
 
 template <int S>
-__global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) {
+__global__ void __launch_bounds__(kThreads) k_scatter_stable(SceneDev sc, FrameDev fr) {
     if (fr.status[kStatOverflow]) return;
     extern __shared__ __align__(16) unsigned char s_raw[];
     float4 *s_rec = reinterpret_cast<float4 *>(s_raw);                           // [kThreads]
-    int *s_key = reinterpret_cast<int *>(s_rec + kThreads);                      // [kScatterStage]
-    unsigned short *s_slot = reinterpret_cast<unsigned short *>(s_key + kScatterStage);  // [kScatterStage]
+    int *s_key = reinterpret_cast<int *>(s_rec + kThreads);                      // [kStableStage]
+    unsigned short *s_slot = reinterpret_cast<unsigned short *>(s_key + kStableStage);  // [kStableStage]
+    // per staged pair: its slice's leader lane for its tile (5 bits), its rank among the
+    // slice's pairs of that tile (5 bits) and, at the leader, their count (6 bits)
+    unsigned short *s_info = s_slot + kStableStage;                              // [kStableStage]
     // cursor of this chunk's slice of every tile segment, relative to the start of the
     // view's segments (a view holds fewer than 2^31 pairs: the scan checks it)
-    int *s_cur = reinterpret_cast<int *>(s_slot + kScatterStage);               // [g_n][n_tiles]
+    int *s_cur = reinterpret_cast<int *>(s_info + kStableStage);                // [g_n][n_tiles]
     __shared__ ViewParams s_view[kMaxGroup];
     __shared__ int64_t s_vbase[kMaxGroup];
     __shared__ int64_t s_tb[kMaxTypes + 1];
@@ -686,8 +846,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
             float4 *lists = fr.lists + s_vbase[g];
             int *pids = fr.pids ? fr.pids + s_vbase[g] : nullptr;
             int *cur = s_cur + g * nt;
-            for (int w0 = 0; w0 < M; w0 += kScatterStage) {
-                const int m = min(kScatterStage, M - w0);
+            for (int w0 = 0; w0 < M; w0 += kStableStage) {
+                const int m = min(kStableStage, M - w0);
                 // ---- 2. stage this window's pairs, in particle order
                 if (mask) {
                     const int t00 = ty0 * vp.ntx + tx0;
@@ -711,26 +871,44 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
                                       warp * 32 + src, s_key, s_slot, lane);
                 }
                 __syncthreads();
-                // ---- 3. slots in order: one warp, 32 staged pairs per step
+                // ---- 3a. per 32-pair slice: the pairs of each tile and their ranks
+                for (int j0 = warp * 32; j0 < m; j0 += kThreads) {
+                    const int j = j0 + lane;
+                    const uint32_t t = j < m ? (uint32_t)s_key[j] : kNoTile;
+                    uint32_t peers = 0xffffffffu;
+#pragma unroll
+                    for (int bit = 0; bit < kTileKeyBits; ++bit) {
+                        const uint32_t on = (t >> bit) & 1u;
+                        const uint32_t bal = __ballot_sync(0xffffffffu, on);
+                        peers &= on ? bal : ~bal;
+                    }
+                    const int leader = __ffs(peers) - 1;
+                    if (j < m)
+                        s_info[j] = (unsigned short)(leader | (__popc(peers & lt) << 5) |
+                                                     ((lane == leader ? __popc(peers) : 0) << 10));
+                }
+                __syncthreads();
+                // ---- 3b. slice bases in order: one warp; each slice's leader of a tile
+                // takes its pairs' slots from the cursor and leaves the first in s_key
                 if (warp == 0) {
                     for (int j0 = 0; j0 < m; j0 += 32) {
                         const int j = j0 + lane;
-                        const int t = j < m ? s_key[j] : -1;
-                        const uint32_t peers = __match_any_sync(0xffffffffu, t);
-                        const int leader = __ffs(peers) - 1;
-                        int base = 0;
-                        if (j < m && lane == leader) {
-                            base = cur[t];
-                            cur[t] = base + __popc(peers);
+                        if (j < m) {
+                            const int c = (int)(s_info[j] >> 10);
+                            if (c) {
+                                const int t = s_key[j];
+                                const int base = cur[t];
+                                cur[t] = base + c;
+                                s_key[j] = base;
+                            }
                         }
-                        base = __shfl_sync(0xffffffffu, base, leader);
-                        if (j < m) s_key[j] = base + __popc(peers & lt);
                     }
                 }
                 __syncthreads();
-                // ---- 4. records to their slots
+                // ---- 4. records to their slots: the leader's base plus the rank
                 for (int j = tid; j < m; j += kThreads) {
-                    const int pos = s_key[j];
+                    const uint32_t inf = s_info[j];
+                    const int pos = s_key[(j & ~31) + (int)(inf & 31u)] + (int)((inf >> 5) & 31u);
                     const int sl = s_slot[j];
                     lists[pos] = s_rec[sl];
                     if (pids) pids[pos] = (int)(r0 + sl);
@@ -742,16 +920,21 @@ __global__ void __launch_bounds__(kThreads) k_scatter(SceneDev sc, FrameDev fr) 
     }
 }
 
-template <int S> static cudaError_t scatter_impl(const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
-    const size_t smem = (size_t)fr.G * fr.n_tiles * sizeof(int) + kScatterExtra;
-    cudaError_t err = ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax + kScatterExtra);
+template <int S> static cudaError_t scatter_stable_impl(const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
+    const size_t smem = (size_t)fr.G * fr.n_tiles * sizeof(int) + kStableExtra;
+    cudaError_t err = ensure_smem_limit((const void *)k_scatter_stable<S>, kBinSmemMax + kStableExtra);
     if (err != cudaSuccess) return err;
     dim3 grid(fr.n_chunks, (fr.V + fr.G - 1) / fr.G);
-    k_scatter<S><<<grid, kThreads, smem, st>>>(sc, fr);
+    k_scatter_stable<S><<<grid, kThreads, smem, st>>>(sc, fr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, cudaStream_t st) {
+cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, bool stable, cudaStream_t st) {
+    if (stable) {
+        if (storage == 0) return scatter_stable_impl<0>(sc, fr, st);
+        if (storage == 1) return scatter_stable_impl<1>(sc, fr, st);
+        return scatter_stable_impl<2>(sc, fr, st);
+    }
     if (storage == 0) return scatter_impl<0>(sc, fr, st);
     if (storage == 1) return scatter_impl<1>(sc, fr, st);
     return scatter_impl<2>(sc, fr, st);
@@ -762,10 +945,9 @@ cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, 
 template <int S> static int bin_occupancy(size_t smem) {
     int a = 0, b = 0;
     if (ensure_smem_limit((const void *)k_count<S>, kBinSmemMax) != cudaSuccess ||
-        ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax + kScatterExtra) != cudaSuccess ||
+        ensure_smem_limit((const void *)k_scatter<S>, kBinSmemMax) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_count<S>, kThreads, smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scatter<S>, kThreads, smem + kScatterExtra) !=
-            cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scatter<S>, kThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }

@@ -72,7 +72,7 @@ __device__ __forceinline__ void put_pixel(float *p, float a, int mode) {
 template <int NR, int NC>
 __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDev fr, int *queue, float *out,
                                                          int out_accum) {
-    if (fr.status[kStatOverflow]) return;
+    if (fr.status[kStatOverflow] || fr.status[kStatTimeout]) return;  // no complete tile lists
     extern __shared__ __align__(16) unsigned char s_raw[];
     __shared__ uint64_t s_bar[2];
     __shared__ int s_item, s_last;
@@ -452,7 +452,7 @@ __device__ __forceinline__ void run_dispatch(int id, const WarpSmem *ws, int j0,
 template <int NR, int NC, bool kViewScale, bool kEmit>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCtas))
     k_splat_warp(SceneDev sc, FrameDev fr, int *queue, float *out, int out_accum, int split) {
-    if (fr.status[kStatOverflow]) return;
+    if (fr.status[kStatOverflow] || fr.status[kStatTimeout]) return;  // no complete tile lists
     extern __shared__ __align__(16) unsigned char s_raw[];
     WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_raw) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -560,7 +560,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                                   range_id(ilo >> 3, ihi >> 3, NC);
                 }
                 // rank among the stage's records of the same rectangle, in record order
-                const uint32_t peers = __match_any_sync(0xffffffffu, rid[q4]);
+                // (lanes with equal rectangle ids, found bit by bit with ballots)
+                uint32_t peers = 0xffffffffu;
+#pragma unroll
+                for (int bit = 0; bit < 6; ++bit) {
+                    const uint32_t on = ((uint32_t)(rid[q4] + 1) >> bit) & 1u;
+                    const uint32_t bal = __ballot_sync(0xffffffffu, on);
+                    peers &= on ? bal : ~bal;
+                }
                 const int leader = __ffs(peers) - 1;
                 int before = 0;
                 if (rid[q4] >= 0 && lane == leader) {

@@ -826,11 +826,12 @@ static splotch_status count_and_size(splotch_scene *sc, const RenderSetup &rs, F
 
 // Enqueue scatter + splat for a sized frame.
 static splotch_status scatter_and_splat(splotch_scene *sc, FrameHost &fh, char *fixed, char *var, float *out,
-                                        int out_accum, int items, cudaStream_t st, cudaEvent_t *ev = nullptr) {
+                                        int out_accum, bool stable, int items, cudaStream_t st,
+                                        cudaEvent_t *ev = nullptr) {
     FrameDev fr = frame_dev(fh, fixed, var);
     CUDA_TRY(cudaMemsetAsync(fixed + fh.o_queue, 0, sizeof(int) * 4, st));
     if (ev) CUDA_TRY(cudaEventRecord(ev[3], st));
-    CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, st));
+    CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, stable, st));
     if (ev) CUDA_TRY(cudaEventRecord(ev[4], st));
     CUDA_TRY(launch_splat(sc->dev_view, fr, (int *)(fixed + fh.o_queue), out, out_accum,
                           splat_grid(sc->dev, fh.T, items), st));
@@ -882,7 +883,7 @@ static splotch_status render_frame(splotch_scene *sc, const RenderSetup &rs, flo
         }
         if (dbg_members) {
             FrameDev fr = frame_dev(fh, fixed, var);
-            cudaError_t e = launch_scatter(sc->storage, sc->dev_view, fr, st);
+            cudaError_t e = launch_scatter(sc->storage, sc->dev_view, fr, true, st);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(dbg_counts, fixed + fh.o_counts, sizeof(int) * fh.n_tiles, cudaMemcpyDeviceToDevice, st);
             if (e == cudaSuccess)
@@ -894,7 +895,8 @@ static splotch_status render_frame(splotch_scene *sc, const RenderSetup &rs, flo
             if (e != cudaSuccess) s = fail(SPLOTCH_ERR_CUDA, "debug bins: %s", cudaGetErrorString(e));
             break;
         }
-        s = scatter_and_splat(sc, fh, fixed, var, out, out_mode(rs.pr.flags), items, st, ev);
+        s = scatter_and_splat(sc, fh, fixed, var, out, out_mode(rs.pr.flags), (rs.pr.flags & SPLOTCH_STABLE) != 0,
+                              items, st, ev);
         if (s != SPLOTCH_OK) break;
         if (sync) {
             int64_t *box = host_box();
@@ -1017,7 +1019,7 @@ static splotch_status plan_enqueue(splotch_plan *pl, float *out, cudaStream_t st
     CUDA_TRY(cudaMemsetAsync(pl->fixed + fh.o_queue, 0, sizeof(int) * 4, st));
     CUDA_TRY(launch_count(sc->storage, sc->dev_view, fr, st));
     CUDA_TRY(launch_scan(fr, target_items(sc->dev, fh.T), kMinItemPairs, st));
-    CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, st));
+    CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, (pl->rs.pr.flags & SPLOTCH_STABLE) != 0, st));
     CUDA_TRY(launch_splat(sc->dev_view, fr, (int *)(pl->fixed + fh.o_queue), out,
                           out_mode(pl->rs.pr.flags), pl->grid, st));
     CUDA_TRY(cudaMemcpyAsync(pl->box, pl->fixed + fh.o_sizes, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, st));
@@ -1398,7 +1400,7 @@ extern "C" splotch_status splotch_render_noalloc(splotch_scene *sc, const splotc
     CUDA_TRY(cudaMemsetAsync(var + fh.o_scratch, 0, fh.var_bytes - fh.o_scratch, st));
     CUDA_TRY(launch_count(sc->storage, sc->dev_view, fr, st));
     CUDA_TRY(launch_scan(fr, target_items(sc->dev, T), kMinItemPairs, st));
-    CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, st));
+    CUDA_TRY(launch_scatter(sc->storage, sc->dev_view, fr, (pr.flags & SPLOTCH_STABLE) != 0, st));
     CUDA_TRY(launch_splat(sc->dev_view, fr, (int *)(base + fh.o_queue), out,
                           out_mode(pr.flags), sm_count(dev) * std::max(1, splat_blocks_per_sm(T)), st));
     int64_t sizes[8];

@@ -237,6 +237,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+// Plain arrival (release semantics at CTA scope: this thread's earlier shared-memory
+// writes are visible to a thread whose wait observes the phase completing).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -248,6 +253,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Non-blocking test of a phase's completion.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
@@ -325,7 +340,9 @@ cudaError_t launch_prepare(const float *x, const float *y, const float *z, const
                            cudaStream_t st);
 cudaError_t launch_count(int storage, const SceneDev &sc, const FrameDev &fr, cudaStream_t st);
 cudaError_t launch_scan(const FrameDev &fr, int target_items, int kmin, cudaStream_t st);
-cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, cudaStream_t st);
+// stable: every tile list in ascending particle index (k_scatter_stable); else each
+// chunk's members in arrival order (k_scatter)
+cudaError_t launch_scatter(int storage, const SceneDev &sc, const FrameDev &fr, bool stable, cudaStream_t st);
 cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, float *out,
                          int out_accum, int grid, cudaStream_t st);
 int splat_blocks_per_sm(int T);

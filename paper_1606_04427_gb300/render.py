@@ -23,7 +23,9 @@ class RenderParams:
     support in pixels; ``accum`` returns the accumulation a instead of 1 - exp(-a);
     ``add`` adds the accumulation to what the output holds; ``sync`` waits for the frame
     and reports device-side timeouts; ``map`` makes the depth-ordered render write the
-    per-pixel affine map (alpha, beta) instead of I."""
+    per-pixel affine map (alpha, beta) instead of I; ``stable`` builds every tile list in
+    ascending particle index, which makes the image bitwise reproducible (the binning
+    takes longer)."""
     tile: int = 0
     rfac: float = 0.75
     sigma_over_R: float = 0.5
@@ -35,6 +37,7 @@ class RenderParams:
     graph: bool = False
     timing: bool = False
     map: bool = False
+    stable: bool = False
 
     def c(self) -> _lib.RenderParamsC:
         p = _lib.RenderParamsC()
@@ -45,7 +48,8 @@ class RenderParams:
         p.block_particles = int(self.block_particles)
         p.flags = ((_lib.OUT_ACCUM if self.accum else 0) | (_lib.SYNC if self.sync else 0)
                    | (_lib.PLAN_GRAPH if self.graph else 0) | (_lib.TIMING if self.timing else 0)
-                   | (_lib.OUT_ADD if self.add else 0) | (_lib.OUT_MAP if self.map else 0))
+                   | (_lib.OUT_ADD if self.add else 0) | (_lib.OUT_MAP if self.map else 0)
+                   | (_lib.STABLE if self.stable else 0))
         return p
 
 

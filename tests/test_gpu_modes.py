@@ -207,26 +207,61 @@ def test_streamed_render_equals_resident_render():
     assert torch.allclose(acc, whole_acc, rtol=2e-5, atol=1e-7)
 
 
+def _max_contributions(ps, cam):
+    """Largest number of particles covering one pixel (the oracle's FP32 raster and the
+    coverage rule d^2 < R^2), for the summation-order bound."""
+    r = oracle.raster(ps, cam)
+    a = r["active"]
+    X, Y, R = (r[k][a].astype(np.float32) for k in ("X", "Y", "R"))
+    cnt = np.zeros((cam.height, cam.width), np.int64)
+    for x, y, rr in zip(X, Y, R):
+        i0, i1 = max(0, int(np.ceil(x - rr - 0.5)) - 1), min(cam.width - 1, int(np.floor(x + rr - 0.5)) + 1)
+        j0, j1 = max(0, int(np.ceil(y - rr - 0.5)) - 1), min(cam.height - 1, int(np.floor(y + rr - 0.5)) + 1)
+        if i0 > i1 or j0 > j1:
+            continue
+        px = np.arange(i0, i1 + 1, dtype=np.float32) + np.float32(0.5)
+        py = np.arange(j0, j1 + 1, dtype=np.float32) + np.float32(0.5)
+        dx2 = (px - x) * (px - x)
+        dy2 = (py - y) * (py - y)
+        cnt[j0:j1 + 1, i0:i1 + 1] += (dy2[:, None] + dx2[None, :]) < rr * rr
+    return int(cnt.max())
+
+
+# A pixel's accumulation is a sum of n non-negative FP32 terms (Section 3.2.2: colour x
+# scalar weight).  Without SPLOTCH_STABLE the order of the terms inside one chunk's part
+# of a tile list may change from run to run (the reading that the summation order inside
+# a pixel is free), and any order's FP32 sum lies within (n - 1) 2^-24 of the exact sum,
+# relative; the tests below derive their bounds from that.
+U32 = 2.0 ** -24
+
+
 def test_additive_output_sums_renders():
     """SPLOTCH_OUT_ADD adds the accumulation to the output: two additive renders of the
-    same frame give twice the accumulation.  Renders are deterministic (tile lists in
-    particle order, split tiles merged exactly), so the sum is exactly 2 a."""
+    same frame give twice the accumulation, exactly with stable tile lists, and within the
+    summation-order bound (4 (n - 1) + 2) 2^-24 relative without them."""
     ps = synth.clustered_set(30000, 12, grid=32).with_brightness([0.05])
     cam = synth.front_camera(128, 96)
     sc = render.Scene(ps, "f32")
-    acc = sc.render(cam, render.RenderParams(accum=True))
+    acc = sc.render(cam, render.RenderParams(accum=True, stable=True))
     out = torch.zeros_like(acc)
-    sc.render(cam, render.RenderParams(add=True), out)
-    sc.render(cam, render.RenderParams(add=True), out)
+    sc.render(cam, render.RenderParams(add=True, stable=True), out)
+    sc.render(cam, render.RenderParams(add=True, stable=True), out)
     assert torch.equal(out, 2 * acc)
+    n = _max_contributions(ps, cam)
+    rtol = (4 * (n - 1) + 2) * U32
+    out.zero_()
+    sc.render(cam, render.RenderParams(add=True), out)
+    sc.render(cam, render.RenderParams(add=True), out)
+    assert torch.allclose(out, 2 * acc, rtol=rtol, atol=0.0), (n, rtol)
 
 
 @pytest.mark.parametrize("T", [8, 16, 24, 32, 40, 64])
 def test_renders_are_bitwise_reproducible(T):
-    """The same frame rendered again, with other work in between and a different number of
-    particle chunks, gives the same bits: every tile list is in ascending particle index
-    and the slices of a split tile merge exactly, so no summation order depends on which
-    CTA or warp runs first."""
+    """With stable tile lists the same frame rendered again, with other work in between
+    and a different number of particle chunks, gives the same bits: every tile list is in
+    ascending particle index and the slices of a split tile merge exactly, so no
+    summation order depends on which CTA or warp runs first.  Without them a render stays
+    within the summation-order bound of the stable one."""
     rng = np.random.default_rng(31)
     ps = synth.two_species_set(40000, 15000, 17, grid=32).with_brightness([0.05, 0.3])
     # a crowded spot: its tiles are split over several work items
@@ -235,13 +270,15 @@ def test_renders_are_bitwise_reproducible(T):
     ps.y[:k] = 0.5 + rng.normal(0, 0.002, k)
     sc = render.Scene(ps, "f32")
     cam = synth.front_camera(200, 150)
-    p = render.RenderParams(tile=T, accum=True)
-    first = sc.render(cam, p).clone()
+    first = sc.render(cam, render.RenderParams(tile=T, accum=True, stable=True)).clone()
     other = render.Scene(synth.plain_set(5000, 3), "f32")
     other.render(synth.front_camera(64, 64))
     for bp in (0, 4096, 30000):
-        again = sc.render(cam, render.RenderParams(tile=T, accum=True, block_particles=bp))
+        again = sc.render(cam, render.RenderParams(tile=T, accum=True, stable=True, block_particles=bp))
         assert torch.equal(first, again), (T, bp)
+    n = _max_contributions(ps, cam)
+    fast = sc.render(cam, render.RenderParams(tile=T, accum=True))
+    assert torch.allclose(fast, first, rtol=(2 * (n - 1) + 2) * U32, atol=0.0), (T, n)
 
 
 def test_plan_per_view_brightness_matches_rescaled_scenes():
