@@ -338,6 +338,32 @@ splotch_status splotch_plan_destroy(splotch_plan *plan);
 int64_t splotch_workspace_bytes(const splotch_scene *scene, int32_t width, int32_t height,
                                 int32_t tile, int64_t pairs);
 
+/* Two-phase render of one view, for callers that share the device and must know a
+ * frame's memory before it is taken (a request server admitting work by HBM footprint).
+ * The phases are those of splotch_render: the count pass of the binning (Section 3.2.1:
+ * every particle's member tiles, counted per tile), then the lists and the splat.
+ *   splotch_frame_fixed_bytes: device bytes the count phase allocates for this scene,
+ *     camera and parameters (-1 on invalid arguments).  No GPU work.
+ *   splotch_frame_prepare: allocates those bytes (the scene's allocator, stream-ordered
+ *     on `stream`), runs raster + count + scan and waits for them; returns the frame,
+ *     its fixed bytes, the exact bytes splotch_frame_render will allocate (*var_bytes:
+ *     the frame's tile lists and split-tile scratch) and its particle-tile pairs.
+ *   splotch_frame_render: allocates exactly *var_bytes, then scatter + splat + final
+ *     transform into `out` (device, H x W x 3 FP32, or as params->flags ask), ordered
+ *     after the prepare stream; asynchronous unless SPLOTCH_SYNC.  Once per frame.
+ *   splotch_frame_destroy: releases both allocations, ordered on the stream last used;
+ *     NULL is accepted.
+ * The caller owns `out`; the frame owns its workspace.  Errors as splotch_render;
+ * INVALID_ARG when a frame is rendered twice. */
+typedef struct splotch_frame splotch_frame;
+int64_t splotch_frame_fixed_bytes(const splotch_scene *scene, const splotch_camera *cam,
+                                  const splotch_render_params *params);
+splotch_status splotch_frame_prepare(splotch_scene *scene, const splotch_camera *cam,
+                                     const splotch_render_params *params, void *stream, splotch_frame **frame,
+                                     int64_t *fixed_bytes, int64_t *var_bytes, int64_t *pairs);
+splotch_status splotch_frame_render(splotch_frame *frame, float *out, void *stream);
+splotch_status splotch_frame_destroy(splotch_frame *frame);
+
 /* Self-test of the bounded device wait every kernel uses: one CTA waits on a shared-memory
  * mbarrier that nothing completes, gives up after ~limit_cycles SM cycles (1e3..1e10) and
  * reports it.  Returns SPLOTCH_ERR_TIMEOUT when the wait ran out as designed, SPLOTCH_OK

@@ -90,6 +90,12 @@ SIGNATURES = {
                                  C.c_void_p, C.c_void_p], C.c_int),
     "splotch_render_noalloc": ([C.c_void_p, C.POINTER(CameraC), C.POINTER(RenderParamsC), C.c_void_p,
                                 C.c_void_p], C.c_int),
+    "splotch_frame_fixed_bytes": ([C.c_void_p, C.POINTER(CameraC), C.POINTER(RenderParamsC)], C.c_int64),
+    "splotch_frame_prepare": ([C.c_void_p, C.POINTER(CameraC), C.POINTER(RenderParamsC), C.c_void_p,
+                               C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                               C.POINTER(C.c_int64)], C.c_int),
+    "splotch_frame_render": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "splotch_frame_destroy": ([C.c_void_p], C.c_int),
     "splotch_status_string": ([C.c_int], C.c_char_p),
     "splotch_last_error": ([], C.c_char_p),
 }

@@ -983,6 +983,100 @@ extern "C" int64_t splotch_workspace_bytes(const splotch_scene *sc, int32_t widt
 }
 
 // -----------------------------------------------------------------------------------------
+// two-phase frame: the count pass first, with the exact workspace of the rest reported,
+// so that a caller sharing the device (a request server) can reserve it before the
+// library allocates it
+
+struct splotch_frame {
+    splotch_scene *sc = nullptr;
+    RenderSetup rs;
+    FrameHost fh;
+    char *fixed = nullptr, *var = nullptr;
+    cudaStream_t st = nullptr;
+    int64_t sizes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+extern "C" int64_t splotch_frame_fixed_bytes(const splotch_scene *sc, const splotch_camera *cam,
+                                             const splotch_render_params *params) {
+    if (!sc || !cam) return -1;
+    RenderSetup rs;
+    if (setup_views(cam, 1, params, rs) != SPLOTCH_OK) return -1;
+    FrameHost fh;
+    layout_fixed(fh, sc, 1, rs.views[0].n_tiles, rs.T, rs.pr.block_particles);
+    return (int64_t)fh.fixed_bytes;
+}
+
+extern "C" splotch_status splotch_frame_prepare(splotch_scene *sc, const splotch_camera *cam,
+                                                const splotch_render_params *params, void *stream,
+                                                splotch_frame **out, int64_t *fixed_bytes, int64_t *var_bytes,
+                                                int64_t *pairs) {
+    if (!sc || !cam || !out) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    splotch_frame *f = new splotch_frame();
+    f->sc = sc;
+    f->st = (cudaStream_t)stream;
+    splotch_status s = setup_views(cam, 1, params, f->rs);
+    if (s != SPLOTCH_OK) {
+        delete f;
+        return s;
+    }
+    layout_fixed(f->fh, sc, 1, f->rs.views[0].n_tiles, f->rs.T, f->rs.pr.block_particles);
+    f->fixed = (char *)sc->mem.alloc(f->fh.fixed_bytes, f->st);
+    if (!f->fixed) {
+        delete f;
+        return fail(SPLOTCH_ERR_OOM, "frame workspace (%zu bytes)", f->fh.fixed_bytes);
+    }
+    s = count_and_size(sc, f->rs, f->fh, f->fixed, f->st, f->sizes);
+    if (s != SPLOTCH_OK) {
+        splotch_frame_destroy(f);
+        return s;
+    }
+    layout_var(f->fh, f->sizes[kSizePairs], (int)f->sizes[kSizeItems], (int)f->sizes[kSizeSplits], false);
+    if (fixed_bytes) *fixed_bytes = (int64_t)f->fh.fixed_bytes;
+    if (var_bytes) *var_bytes = (int64_t)f->fh.var_bytes;
+    if (pairs) *pairs = f->sizes[kSizePairs];
+    *out = f;
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_frame_render(splotch_frame *f, float *out, void *stream) {
+    if (!f || !out) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    if (f->var) return fail(SPLOTCH_ERR_INVALID_ARG, "frame already rendered");
+    splotch_scene *sc = f->sc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (st != f->st) {  // the workspace was allocated in the order of the prepare stream
+        cudaEvent_t ev = nullptr;
+        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, f->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "stream order: %s", cudaGetErrorString(e));
+        f->st = st;
+    }
+    f->var = (char *)sc->mem.alloc(f->fh.var_bytes, st);
+    if (!f->var) return fail(SPLOTCH_ERR_OOM, "tile lists (%zu bytes)", f->fh.var_bytes);
+    CUDA_TRY(cudaMemsetAsync(f->var + f->fh.o_scratch, 0, f->fh.var_bytes - f->fh.o_scratch, st));
+    splotch_status s = scatter_and_splat(sc, f->fh, f->fixed, f->var, out, out_mode(f->rs.pr.flags),
+                                         (f->rs.pr.flags & SPLOTCH_STABLE) != 0, (int)f->sizes[kSizeItems], st);
+    if (s != SPLOTCH_OK || !(f->rs.pr.flags & SPLOTCH_SYNC)) return s;
+    int64_t *box = host_box();
+    if (!box) return fail(SPLOTCH_ERR_OOM, "pinned host buffer");
+    cudaError_t e = cudaMemcpyAsync(box, f->fixed + f->fh.o_status, sizeof(int) * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "render: %s", cudaGetErrorString(e));
+    if (((const int *)box)[kStatTimeout]) return fail(SPLOTCH_ERR_TIMEOUT, "splat stage wait timed out");
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_frame_destroy(splotch_frame *f) {
+    if (!f) return SPLOTCH_OK;
+    if (f->var) f->sc->mem.release(f->var, f->st);
+    if (f->fixed) f->sc->mem.release(f->fixed, f->st);
+    delete f;
+    return SPLOTCH_OK;
+}
+
+// -----------------------------------------------------------------------------------------
 // plan: pre-sized multi-view frame, launchable without host synchronisation
 
 struct splotch_plan {

@@ -218,6 +218,27 @@ class Scene:
                                        _stream_handle(stream)), "render")
         return out[0] if single and out.dim() == 4 else out
 
+    def frame_fixed_bytes(self, cam, params: Optional[RenderParams] = None) -> int:
+        """Device bytes the count phase of a two-phase render allocates (no GPU work)."""
+        p = (params or RenderParams()).c()
+        c = _lib.camera_c(cam)
+        n = int(self._lib.splotch_frame_fixed_bytes(self.handle, C.byref(c), C.byref(p)))
+        if n < 0:
+            raise ValueError("invalid camera or parameters")
+        return n
+
+    def prepare(self, cam, params: Optional[RenderParams] = None, stream=None) -> "Frame":
+        """Count phase of one view (splotch_frame_prepare): returns a :class:`Frame` that
+        knows the exact device bytes its render will allocate."""
+        p = (params or RenderParams()).c()
+        c = _lib.camera_c(cam)
+        h = C.c_void_p()
+        fixed, var, pairs = C.c_int64(), C.c_int64(), C.c_int64()
+        check(self._lib.splotch_frame_prepare(self.handle, C.byref(c), C.byref(p), _stream_handle(stream),
+                                              C.byref(h), C.byref(fixed), C.byref(var), C.byref(pairs)),
+              "frame_prepare")
+        return Frame(self, h, cam, int(fixed.value), int(var.value), int(pairs.value))
+
     def render_noalloc(self, cam, out: torch.Tensor, params: Optional[RenderParams] = None,
                        stream=None) -> torch.Tensor:
         """Render one camera into ``out`` (H x W x 3 FP32, on the device) without any
@@ -299,6 +320,39 @@ class Scene:
     def close(self):
         if getattr(self, "_h", None) is not None:
             self._lib.splotch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Frame:
+    """A prepared view (count phase done): ``fixed_bytes`` held now, ``var_bytes`` the
+    exact device bytes :meth:`render` allocates, ``pairs`` its particle-tile pairs."""
+
+    def __init__(self, scene: "Scene", handle, cam, fixed_bytes: int, var_bytes: int, pairs: int):
+        self.scene = scene
+        self._h = handle
+        self.camera = cam
+        self.fixed_bytes = fixed_bytes
+        self.var_bytes = var_bytes
+        self.pairs = pairs
+
+    def render(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Scatter + splat into ``out`` (H x W x 3 FP32 on the device)."""
+        H, W = int(self.camera.height), int(self.camera.width)
+        if out is None:
+            out = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == H * W * 3
+        check(self.scene._lib.splotch_frame_render(self._h, out.data_ptr(), _stream_handle(stream)), "frame_render")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.scene._lib.splotch_frame_destroy(self._h)
             self._h = None
 
     def __del__(self):

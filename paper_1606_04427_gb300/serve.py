@@ -1,11 +1,19 @@
 """Continuous-batching render server over particle sets resident on the GPU.
 
 Requests (set, camera) arrive at any time.  A request is admitted when a slot (a
-worker thread with its own CUDA stream) is free and its estimated device footprint
-(frame workspace + tile lists + image) fits in the remaining HBM budget; admitted
-requests render concurrently on their streams, so a request that arrives while
-others are on the GPU starts as soon as a slot and memory free up.  Latency is
-arrival to completion; the server reports throughput and p50 / p99.
+worker thread with its own CUDA stream) is free and its device footprint fits in the
+remaining HBM budget; admitted requests render concurrently on their streams, so a
+request that arrives while others are on the GPU starts as soon as a slot and memory
+free up.  Latency is arrival to completion; the server reports throughput and p50 / p99.
+
+Admission is a reservation of exactly what the library will allocate, never an
+estimate.  A request first reserves the count phase's workspace and its image (both
+known before any GPU work), runs the count phase (splotch_frame_prepare), which reports
+the exact bytes of its tile lists, and reserves those before the library allocates
+them.  When they do not fit, the request releases everything and waits in the queue
+with its full footprint known; the next admission reserves all of it at once.  The sum
+of reservations stays within the budget, except for a request admitted with nothing
+else in flight (so that the queue always drains) whose footprint alone exceeds it.
 
 The paper's analogue is several MPI tasks sharing one coprocessor to keep it busy
 (Section 3.2.1, Section 4.2.1); here the tasks are streams of one process.
@@ -35,6 +43,7 @@ class Completed:
     finish: float
     pairs: int
     reserved_bytes: int
+    allocated_bytes: int = 0
     image: Optional[torch.Tensor] = None
 
     @property
@@ -48,8 +57,13 @@ class _Pending:
     set_index: int
     camera: object
     arrival: float
-    estimate: int = 0
+    first: int = 0           # count-phase workspace + image: known at submission
+    lists: Optional[int] = None  # tile lists and split scratch, once a count phase ran
     bypassed: int = 0
+
+    @property
+    def need(self) -> int:
+        return self.first + (self.lists or 0)
 
 
 class Server:
@@ -66,13 +80,12 @@ class Server:
             free, _ = torch.cuda.mem_get_info()
             hbm_budget = int(0.8 * free)
         self.budget = int(hbm_budget)
-        base = params or render.RenderParams()
-        self.params = render.RenderParams(**{**base.__dict__, "timing": True})
+        self.params = params or render.RenderParams()
         self.keep_images = keep_images
         self.max_bypass = max_bypass
         self.reserved = 0
         self.peak_reserved = 0
-        self.ratio: Dict[tuple, float] = {}
+        self.requeued = 0
         self.cv = threading.Condition()
         self.queue: deque = deque()
         self.done: List[Completed] = []
@@ -88,25 +101,13 @@ class Server:
             t.start()
 
     # ---------------------------------------------------------------------------------
-    def _key(self, set_index, cam):
-        return (set_index, int(cam.width), int(cam.height))
-
-    def estimate(self, set_index: int, cam) -> int:
-        """Device bytes a request is expected to need: the library's workspace for the
-        predicted pair count (largest pairs / particle seen for this set and size,
-        2.0 before any) plus the output image."""
-        sc = self.scenes[set_index]
-        ratio = self.ratio.get(self._key(set_index, cam), 2.0)
-        pairs = int(ratio * max(1, sc.n)) + 1024
-        ws = sc.workspace_bytes(cam.width, cam.height, self.params.tile, pairs)
-        return int(ws) + int(cam.width) * int(cam.height) * 12
-
     def submit(self, set_index: int, cam, arrival: Optional[float] = None) -> int:
+        sc = self.scenes[set_index]
+        first = sc.frame_fixed_bytes(cam, self.params) + int(cam.width) * int(cam.height) * 12
         with self.cv:
             rid = self.next_id
             self.next_id += 1
-            p = _Pending(rid, set_index, cam, self.now() if arrival is None else arrival)
-            p.estimate = self.estimate(set_index, cam)
+            p = _Pending(rid, set_index, cam, self.now() if arrival is None else arrival, first)
             self.queue.append(p)
             self.cv.notify_all()
             return rid
@@ -115,12 +116,12 @@ class Server:
         return time.perf_counter() - self.t0
 
     def _pick(self) -> Optional[_Pending]:
-        """Earliest queued request that fits the free budget; a request passed over
-        `max_bypass` times blocks later ones until it fits.  With nothing in flight
-        the head is admitted whatever its estimate (so no request waits forever)."""
+        """Earliest queued request whose known footprint fits the free budget; a request
+        passed over `max_bypass` times blocks later ones until it fits.  With nothing in
+        flight the head is admitted whatever its footprint (so no request waits forever)."""
         free = self.budget - self.reserved
         for k, p in enumerate(self.queue):
-            if p.estimate <= free or self.in_flight == 0:
+            if p.need <= free or self.in_flight == 0:
                 for q in list(self.queue)[:k]:
                     q.bypassed += 1
                 del self.queue[k]
@@ -128,6 +129,10 @@ class Server:
             if p.bypassed >= self.max_bypass:
                 return None
         return None
+
+    def _reserve(self, n: int) -> None:
+        self.reserved += n
+        self.peak_reserved = max(self.peak_reserved, self.reserved)
 
     def _worker(self, k: int):
         torch.cuda.set_device(self.device)
@@ -142,31 +147,58 @@ class Server:
                     self.cv.wait(timeout=0.05)
                 if p is None:
                     return
-                self.reserved += p.estimate
-                self.peak_reserved = max(self.peak_reserved, self.reserved)
+                held = p.need  # the first part, and the lists when a count phase already ran
+                alone = self.in_flight == 0
+                self._reserve(held)
                 self.in_flight += 1
             start = self.now()
-            pairs = 0
+            frame = None
             img = None
+            requeue = False
             try:
+                sc = self.scenes[p.set_index]
                 cam = p.camera
-                with torch.cuda.stream(stream):
-                    img = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
-                self.scenes[p.set_index].render([cam], self.params, img, stream=stream)
-                pairs = render.last_timing()["pairs"]
+                frame = sc.prepare(cam, self.params, stream=stream)
+                with self.cv:
+                    if p.lists is not None and frame.var_bytes > p.lists:
+                        # cannot happen (the count phase is deterministic); stay exact anyway
+                        self._reserve(frame.var_bytes - p.lists)
+                        held += frame.var_bytes - p.lists
+                    if p.lists is None:
+                        # the count phase's exact list bytes: reserve them now if they
+                        # fit, else give everything back and wait with the full footprint
+                        if self.reserved + frame.var_bytes <= self.budget or alone:
+                            self._reserve(frame.var_bytes)
+                            held += frame.var_bytes
+                        else:
+                            requeue = True
+                    p.lists = frame.var_bytes
+                if not requeue:
+                    with torch.cuda.stream(stream):
+                        img = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+                    frame.render(img, stream=stream)
+                    stream.synchronize()
             except Exception as e:  # a failed request is reported, the server keeps going
                 with self.cv:
                     self.errors.append(f"request {p.request_id}: {e}")
+            finally:
+                if frame is not None:
+                    fixed, var, pairs = frame.fixed_bytes, frame.var_bytes, frame.pairs
+                    frame.close()
+                    stream.synchronize()
             finish = self.now()
             with self.cv:
-                self.reserved -= p.estimate
+                self.reserved -= held
                 self.in_flight -= 1
-                key = self._key(p.set_index, p.camera)
-                n = max(1, self.scenes[p.set_index].n)
-                self.ratio[key] = max(self.ratio.get(key, 0.0), pairs / n)
-                self.done.append(Completed(p.request_id, p.set_index, int(p.camera.width),
-                                           int(p.camera.height), p.arrival, start, finish, pairs,
-                                           p.estimate, img[0] if (self.keep_images and img is not None) else None))
+                if requeue:
+                    p.bypassed = 0
+                    self.queue.appendleft(p)
+                    self.requeued += 1
+                elif frame is not None:
+                    self.done.append(Completed(p.request_id, p.set_index, int(p.camera.width),
+                                               int(p.camera.height), p.arrival, start, finish, pairs, held,
+                                               fixed + var + int(p.camera.width) * int(p.camera.height) * 12,
+                                               img if (self.keep_images and img is not None) else None))
                 self.cv.notify_all()
 
     def wait_all(self, timeout: Optional[float] = None) -> None:

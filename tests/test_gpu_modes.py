@@ -105,6 +105,43 @@ def test_server_admission_by_footprint():
     assert all(d.reserved_bytes > 0 for d in srv.done)
 
 
+def test_server_reserves_exactly_what_the_library_allocates():
+    """A budget just above the largest request's true footprint (count-phase workspace +
+    tile lists + image, from the two-phase API): the queue drains without errors, the
+    reservations never exceed the budget, and every request reserved exactly the bytes the
+    library and its image took.  The frames still match the plain render."""
+    sets, reqs = _served_sets()
+    scenes = [render.Scene(p, "f16") for p in sets]
+    foot = []
+    for r in reqs:
+        sc = scenes[r.set_index]
+        f = sc.prepare(r.camera)
+        assert f.fixed_bytes == sc.frame_fixed_bytes(r.camera)
+        foot.append(f.fixed_bytes + f.var_bytes + r.camera.width * r.camera.height * 12)
+        img = f.render()
+        torch.cuda.synchronize()
+        want = sc.render(r.camera, render.RenderParams(sync=True))
+        assert torch.allclose(img, want, rtol=0, atol=1e-4)
+        f.close()
+    budget = max(foot) + (1 << 20)
+    srv = serve.Server(scenes, slots=4, hbm_budget=budget)
+    try:
+        for r in reqs:
+            srv.submit(r.set_index, r.camera)
+        srv.wait_all(timeout=120)
+    finally:
+        srv.close()
+    assert not srv.errors, srv.errors
+    assert len(srv.done) == len(reqs)
+    assert srv.peak_reserved <= budget, (srv.peak_reserved, budget)
+    for d in srv.done:
+        assert d.reserved_bytes == d.allocated_bytes == foot[d.request_id], d
+    with pytest.raises(_lib.SplotchError):
+        f = scenes[0].prepare(reqs[0].camera)
+        f.render()
+        f.render()  # a frame renders once
+
+
 def test_shards_sum_to_the_whole_frame():
     """Linearity of the accumulation: rendering two particle shards and summing equals
     rendering all of them (the multi-GPU exchange, checked on one GPU)."""
