@@ -875,13 +875,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_stable(SceneDev sc, FrameD
                 for (int j0 = warp * 32; j0 < m; j0 += kThreads) {
                     const int j = j0 + lane;
                     const uint32_t t = j < m ? (uint32_t)s_key[j] : kNoTile;
-                    uint32_t peers = 0xffffffffu;
-#pragma unroll
-                    for (int bit = 0; bit < kTileKeyBits; ++bit) {
-                        const uint32_t on = (t >> bit) & 1u;
-                        const uint32_t bal = __ballot_sync(0xffffffffu, on);
-                        peers &= on ? bal : ~bal;
-                    }
+                    const uint32_t peers = warp_peers<kTileKeyBits>(t);
                     const int leader = __ffs(peers) - 1;
                     if (j < m)
                         s_info[j] = (unsigned short)(leader | (__popc(peers & lt) << 5) |

@@ -8,7 +8,8 @@
 //
 // One pass over 8 key bits:
 //   k_digit_hist   each CTA counts the digits of its 4096 elements (warp-aggregated
-//                  shared counters), written digit-major: hist[digit * n_blocks + block];
+//                  shared counters: the lanes of equal digit found with ballots), written
+//                  digit-major: hist[digit * n_blocks + block];
 //   k_scan_*       exclusive scan of hist, so hist[d * n_blocks + b] is where block b's
 //                  elements of digit d start in the output;
 //   k_digit_scatter each CTA re-reads its elements and writes them to their slots: an
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const K *__restrict
         const int64_t i = base + r * 32 + lane;
         const bool ok = i < n;
         const uint32_t d = ok ? digit_of(keys[i], shift) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = warp_peers<9>(d);  // digits 0..255, 256 past the end
         if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const K *__restr
         k_r[r] = ok ? keys[i] : (K)0;
         v_r[r] = ok ? vals[i] : 0u;
         const uint32_t d = ok ? digit_of(k_r[r], shift) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = warp_peers<9>(d);  // digits 0..255, 256 past the end
         const int leader = __ffs(peers) - 1;
         uint32_t before = 0;
         if (ok && lane == leader) {

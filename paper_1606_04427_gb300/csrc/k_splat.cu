@@ -561,13 +561,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
                 }
                 // rank among the stage's records of the same rectangle, in record order
                 // (lanes with equal rectangle ids, found bit by bit with ballots)
-                uint32_t peers = 0xffffffffu;
-#pragma unroll
-                for (int bit = 0; bit < 6; ++bit) {
-                    const uint32_t on = ((uint32_t)(rid[q4] + 1) >> bit) & 1u;
-                    const uint32_t bal = __ballot_sync(0xffffffffu, on);
-                    peers &= on ? bal : ~bal;
-                }
+                const uint32_t peers = warp_peers<6>((uint32_t)(rid[q4] + 1));
                 const int leader = __ffs(peers) - 1;
                 int before = 0;
                 if (rid[q4] >= 0 && lane == leader) {

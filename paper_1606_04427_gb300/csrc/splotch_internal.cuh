@@ -207,6 +207,19 @@ __device__ __forceinline__ bool tile_member(const ViewParams &v, float X, float 
     return q < __fmul_rn(thr, thr);
 }
 
+// Lanes of the (full) warp whose key equals this lane's in the low NB bits, found bit by
+// bit with ballots: NB ballots, independent of how many distinct keys the warp holds.
+template <int NB> __device__ __forceinline__ uint32_t warp_peers(uint32_t key) {
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int bit = 0; bit < NB; ++bit) {
+        const uint32_t on = (key >> bit) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, on);
+        peers &= on ? bal : ~bal;
+    }
+    return peers;
+}
+
 // Inclusive warp scan of an int.
 __device__ __forceinline__ int warp_incl_scan_i(int v) {
     const int lane = threadIdx.x & 31;
