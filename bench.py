@@ -11,7 +11,10 @@ storage and FP32 accumulation.
 Workloads: two_species_f16 (default), two_species_f32, two_species_small, clustered,
 plain, two_species_vector_f16 (stars coloured from a per-particle RGB field), batched
 (64 orbit views in one CUDA-graph plan), served (request stream), streamed (out of core
-from host memory), ordered (absorption different from emission, depth-ordered transfer).
+from host memory), ordered (absorption different from emission, depth-ordered transfer),
+ordered_small (the same on the 10 M two-species frame: the small case for profiles).
+The default run also measures the frame with FP32 storage, a 64-view batched plan and a
+short served trace (see extras); --no-extras leaves them out.
 
 Under torchrun (N > 1) every rank renders its own replica of the frame (the
 path needs no collective for independent frames); the step time is the maximum
@@ -439,7 +442,8 @@ def run_ordered(args):
     build.build()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    ps, cam, storage = make_workload("two_species_f16")
+    small = args.workload == "ordered_small"
+    ps, cam, storage = make_workload("two_species_small" if small else "two_species_f16")
     tile = args.tile or render.default_tile(cam.width, cam.height)
     params = render.RenderParams(tile=tile)
     scene = render.Scene(ps, storage)
@@ -473,7 +477,8 @@ def run_ordered(args):
     line = {"metric": METRIC, "value": n / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms, "wall_ms_per_step": wall, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(config_dict("ordered_two_species100M_2048_f16", ps, cam, storage, tile),
+            "config": dict(config_dict("ordered_two_species10M_2048_f16" if small else "ordered_two_species100M_2048_f16",
+                                       ps, cam, storage, tile),
                            absorb=ORDERED_ABSORB),
             "e2e": {"value": n / (e2e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": cam.width * cam.height * 12,
@@ -619,7 +624,7 @@ def main():
         return run_served(args)
     if args.workload == "streamed":
         return run_streamed(args)
-    if args.workload == "ordered":
+    if args.workload in ("ordered", "ordered_small"):
         return run_ordered(args)
 
     import torch

@@ -656,17 +656,25 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
             }
         } else {
             unsigned long long *scr = fr.scratch + (int64_t)slot * 6 * T * T;
+            // the lane's sums go through the warp's (now idle) decode area so that one
+            // loop, not an unrolled copy per pixel, adds them: the splat's straight-line
+            // code already fills the instruction cache
+            float *park = reinterpret_cast<float *>(ws->dec) + lane;  // [NR * NC * 3][32]
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                if (r * 4 + lr >= th) continue;
+            for (int r = 0; r < NR; ++r)
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) {
-                    if (cc * 8 + lc >= tw) continue;
-                    const int pix = (qy + r * 4 + lr) * T + qx + cc * 8 + lc;
-                    fix_add(&scr[2 * pix], ar[r][cc]);
-                    fix_add(&scr[2 * (T * T + pix)], ag[r][cc]);
-                    fix_add(&scr[2 * (2 * T * T + pix)], ab[r][cc]);
+                    const int k = 3 * (r * NC + cc);
+                    park[32 * k] = ar[r][cc];
+                    park[32 * (k + 1)] = ag[r][cc];
+                    park[32 * (k + 2)] = ab[r][cc];
                 }
+#pragma unroll 1
+            for (int k = 0; k < 3 * NR * NC; ++k) {
+                const int ch = k % 3, blk = k / 3, r = blk / NC, cc = blk - r * NC;
+                if (r * 4 + lr >= th || cc * 8 + lc >= tw) continue;
+                const int pix = (qy + r * 4 + lr) * T + qx + cc * 8 + lc;
+                fix_add(&scr[2 * (ch * T * T + pix)], park[32 * k]);
             }
             __threadfence();
             __syncwarp();
