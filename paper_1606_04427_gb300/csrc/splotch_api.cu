@@ -1618,13 +1618,10 @@ extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, i
 
     cudaStream_t side = nullptr;
     CUDA_TRY(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-    cudaEvent_t ready = nullptr;
-    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
-        cudaStreamDestroy(side);
-        return fail(SPLOTCH_ERR_CUDA, "event");
-    }
-    // the previous chunk's scene is released only once its render is ordered behind this one
+    // the previous chunk's scene and frame are released only once its render is ordered
+    // behind this one
     splotch_scene *prev = nullptr;
+    splotch_frame *prevf = nullptr;
     auto drop = [&](splotch_scene *sc) {
         if (!sc) return;
         sc->mem.release(sc->attr, st);
@@ -1632,8 +1629,12 @@ extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, i
         delete sc;
     };
     const float *src[5] = {d->x, d->y, d->z, d->h, d->intensity};
-    for (int64_t b = 0; b < d->n && s == SPLOTCH_OK; b += chunk) {
-        const int64_t len = std::min(chunk, d->n - b);
+    // chunk sizes ramp up from an eighth of `chunk`, doubling: the first transfer, which
+    // nothing can hide, is short, and each later one overlaps the render of a chunk half
+    // its size (the host link moves particles faster than the frame renders them)
+    int64_t step = std::max<int64_t>(1, std::min(chunk, std::max<int64_t>(chunk / 8, (int64_t)1 << 20)));
+    for (int64_t b = 0, len = 0; b < d->n && s == SPLOTCH_OK; b += len, step = std::min(chunk, 2 * step)) {
+        len = std::min(step, d->n - b);
         splotch_scene_desc cd = *d;
         cd.n = len;
         const float *const *p = src;
@@ -1645,22 +1646,28 @@ extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, i
         cd.i_min = lo.data();
         cd.i_max = hi.data();
         cd.stream = side;
-        // prepared on the side stream while the previous chunk's scatter and splat run
+        // copied, prepared and counted (the count phase of a two-phase frame) on the side
+        // stream while the previous chunk's scatter and splat run on `stream`; the host
+        // waits only for the side stream
         splotch_scene *sc = nullptr;
         s = create_scene_impl(&cd, &sc, true);
         if (s != SPLOTCH_OK) break;
-        if (cudaEventRecord(ready, side) != cudaSuccess || cudaStreamWaitEvent(st, ready, 0) != cudaSuccess) {
+        splotch_frame *f = nullptr;
+        s = splotch_frame_prepare(sc, cam, &pr, side, &f, nullptr, nullptr, nullptr);
+        if (s != SPLOTCH_OK) {
             drop(sc);
-            s = fail(SPLOTCH_ERR_CUDA, "stream order");
             break;
         }
-        s = splotch_render(sc, cam, 1, &pr, out, st);
+        // the scatter and splat on `stream`, ordered after the side stream's count
+        s = splotch_frame_render(f, out, st);
+        splotch_frame_destroy(prevf);
         drop(prev);
         prev = sc;
+        prevf = f;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess && s == SPLOTCH_OK) s = fail(SPLOTCH_ERR_CUDA, "streamed render");
+    splotch_frame_destroy(prevf);
     drop(prev);
-    cudaEventDestroy(ready);
     cudaStreamDestroy(side);
     if (s != SPLOTCH_OK) return s;
     if (!keep_accum && !add) {
