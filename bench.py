@@ -176,11 +176,14 @@ SFU_PER_SM = 16
 SPLAT_FLOPS_PER_PAIR = 10
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# kernel, from one ncu capture per workload; valid only while the kernel source hashes
-# to the recorded digest, else reported as null.
+# kernel, from one ncu capture of the small case of the same workload (two_species_small:
+# a tenth of the particles, the same image), scaled to the full launch by the tile records
+# read (204374882 against 20443231; the image write does not scale); valid only while the
+# kernel source hashes to the recorded digest, else reported as null.
 TRAFFIC = {
-    "two_species_f16": {"bytes_per_launch": 3288057600 + 60526336, "digest": "76bcd3177af78893",
-                        "kernel": "k_splat_warp<4,2>", "tile": 16},
+    "two_species_f16": {"bytes_per_launch": round(345598976 * 204374882 / 20443231) + 45143296,
+                        "digest": "4a8b9ea1c9d89c60", "kernel": "k_splat_warp<4,2>", "tile": 16,
+                        "source": "small-case capture scaled by records"},
 }
 
 
