@@ -1039,25 +1039,49 @@ extern "C" splotch_status splotch_frame_prepare(splotch_scene *sc, const splotch
     return SPLOTCH_OK;
 }
 
-extern "C" splotch_status splotch_frame_render(splotch_frame *f, float *out, void *stream) {
-    if (!f || !out) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+// Order stream `st` after everything enqueued so far on the frame's stream, and make `st`
+// the frame's stream (its workspace is released in that order).
+static splotch_status frame_follow(splotch_frame *f, cudaStream_t st) {
+    if (st == f->st) return SPLOTCH_OK;
+    cudaEvent_t ev = nullptr;
+    CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, f->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "stream order: %s", cudaGetErrorString(e));
+    f->st = st;
+    return SPLOTCH_OK;
+}
+
+// The list phase of a prepared frame: its exact list workspace, then the scatter.
+static splotch_status frame_scatter(splotch_frame *f, cudaStream_t st) {
     if (f->var) return fail(SPLOTCH_ERR_INVALID_ARG, "frame already rendered");
-    splotch_scene *sc = f->sc;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (st != f->st) {  // the workspace was allocated in the order of the prepare stream
-        cudaEvent_t ev = nullptr;
-        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        cudaError_t e = cudaEventRecord(ev, f->st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
-        cudaEventDestroy(ev);
-        if (e != cudaSuccess) return fail(SPLOTCH_ERR_CUDA, "stream order: %s", cudaGetErrorString(e));
-        f->st = st;
-    }
-    f->var = (char *)sc->mem.alloc(f->fh.var_bytes, st);
+    splotch_status s = frame_follow(f, st);
+    if (s != SPLOTCH_OK) return s;
+    f->var = (char *)f->sc->mem.alloc(f->fh.var_bytes, st);
     if (!f->var) return fail(SPLOTCH_ERR_OOM, "tile lists (%zu bytes)", f->fh.var_bytes);
     CUDA_TRY(cudaMemsetAsync(f->var + f->fh.o_scratch, 0, f->fh.var_bytes - f->fh.o_scratch, st));
-    splotch_status s = scatter_and_splat(sc, f->fh, f->fixed, f->var, out, out_mode(f->rs.pr.flags),
-                                         (f->rs.pr.flags & SPLOTCH_STABLE) != 0, (int)f->sizes[kSizeItems], st);
+    CUDA_TRY(cudaMemsetAsync(f->fixed + f->fh.o_queue, 0, sizeof(int) * 4, st));
+    CUDA_TRY(launch_scatter(f->sc->storage, f->sc->dev_view, frame_dev(f->fh, f->fixed, f->var),
+                            (f->rs.pr.flags & SPLOTCH_STABLE) != 0, st));
+    return SPLOTCH_OK;
+}
+
+// The splat of a frame whose lists are built, into `out`.
+static splotch_status frame_splat(splotch_frame *f, float *out, cudaStream_t st) {
+    splotch_status s = frame_follow(f, st);
+    if (s != SPLOTCH_OK) return s;
+    CUDA_TRY(launch_splat(f->sc->dev_view, frame_dev(f->fh, f->fixed, f->var), (int *)(f->fixed + f->fh.o_queue),
+                          out, out_mode(f->rs.pr.flags), splat_grid(f->sc->dev, f->fh.T, (int)f->sizes[kSizeItems]),
+                          st));
+    return SPLOTCH_OK;
+}
+
+extern "C" splotch_status splotch_frame_render(splotch_frame *f, float *out, void *stream) {
+    if (!f || !out) return fail(SPLOTCH_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    splotch_status s = frame_scatter(f, st);
+    if (s == SPLOTCH_OK) s = frame_splat(f, out, st);
     if (s != SPLOTCH_OK || !(f->rs.pr.flags & SPLOTCH_SYNC)) return s;
     int64_t *box = host_box();
     if (!box) return fail(SPLOTCH_ERR_OOM, "pinned host buffer");
@@ -1648,7 +1672,9 @@ extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, i
         cd.stream = side;
         // copied, prepared and counted (the count phase of a two-phase frame) on the side
         // stream while the previous chunk's scatter and splat run on `stream`; the host
-        // waits only for the side stream
+        // waits only for the side stream.  (Scattering on the side stream as well was
+        // slower: a scatter CTA needs a whole SM's registers, so it cannot start beside
+        // the splat's resident CTAs.)
         splotch_scene *sc = nullptr;
         s = create_scene_impl(&cd, &sc, true);
         if (s != SPLOTCH_OK) break;
@@ -1658,8 +1684,8 @@ extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, i
             drop(sc);
             break;
         }
-        // the scatter and splat on `stream`, ordered after the side stream's count
-        s = splotch_frame_render(f, out, st);
+        s = frame_scatter(f, st);
+        if (s == SPLOTCH_OK) s = frame_splat(f, out, st);
         splotch_frame_destroy(prevf);
         drop(prev);
         prev = sc;
