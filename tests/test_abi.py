@@ -184,3 +184,34 @@ def test_far_plane_at_or_before_the_near_plane_is_rejected(lib):
     cam.z_far = 0.0
     st, _, p = _lib_camera(lib, cam)
     assert st == 0 and np.isinf(p[4])
+
+
+def test_two_phase_frame_and_compose_maps_reject_bad_arguments(lib):
+    """The two-phase frame and the slab-map composition check their arguments before any
+    GPU work: NULL scene, camera or frame, a frame rendered into NULL, and composition
+    sizes and overlaps."""
+    cam = _lib.camera_c(synth.front_camera(32, 32))
+    p = lib.splotch_default_params()
+    h = C.c_void_p()
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    assert lib.splotch_frame_prepare(None, C.byref(cam), C.byref(p), None, C.byref(h), C.byref(a), C.byref(b),
+                                     C.byref(c)) == _lib.INVALID_ARG
+    assert not h.value
+    assert lib.splotch_frame_fixed_bytes(None, C.byref(cam), C.byref(p)) == -1
+    assert lib.splotch_frame_render(None, C.c_void_p(8), None) == _lib.INVALID_ARG
+    assert lib.splotch_frame_destroy(None) == 0
+    buf = np.zeros(6 * 10 * 2, np.float32)
+    out = np.zeros(6 * 10, np.float32)
+    assert lib.splotch_compose_maps(buf.ctypes.data, 0, 10, out.ctypes.data, None) == _lib.INVALID_ARG
+    assert lib.splotch_compose_maps(buf.ctypes.data, 1, -1, out.ctypes.data, None) == _lib.INVALID_ARG
+    assert lib.splotch_compose_maps(None, 1, 10, out.ctypes.data, None) == _lib.INVALID_ARG
+    # out inside the maps it composes
+    assert lib.splotch_compose_maps(buf.ctypes.data, 2, 10, buf.ctypes.data + 4 * 60, None) == _lib.INVALID_ARG
+    # nothing to compose: accepted without GPU work
+    assert lib.splotch_compose_maps(None, 1, 0, None, None) == 0
+
+
+def test_stable_flag_value_matches_the_header(lib):
+    src = open(os.path.join(ROOT, "include", "splotch.h")).read()
+    m = re.search(r"SPLOTCH_STABLE\s*=\s*(\d+)", src)
+    assert m and int(m.group(1)) == _lib.STABLE == 64

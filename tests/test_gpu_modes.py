@@ -318,6 +318,28 @@ def test_renders_are_bitwise_reproducible(T):
     assert torch.allclose(fast, first, rtol=(2 * (n - 1) + 2) * U32, atol=0.0), (T, n)
 
 
+def test_stable_plan_replays_are_bitwise_equal_and_match_single_views():
+    """A multi-view plan with stable tile lists replays (CUDA graph) to the same bits, and
+    each view matches the view rendered alone within the summation-order bound (the plan
+    cuts its lists into work items for all views at once, so slice boundaries differ)."""
+    ps = synth.two_species_set(30000, 10000, 41, grid=32).with_brightness([0.05, 0.3])
+    cams = synth.orbit_cameras(5, 128, 96)
+    sc = render.Scene(ps, "f32")
+    plan = render.Plan(sc, cams, render.RenderParams(accum=True, stable=True), graph=True)
+    out = plan.new_output()
+    plan.launch(out)
+    plan.check()
+    first = out.clone()
+    for _ in range(2):
+        plan.launch(out)
+        plan.check()
+        assert torch.equal(out, first)
+    for v, cam in enumerate(cams):
+        alone = sc.render(cam, render.RenderParams(accum=True, stable=True))
+        n = _max_contributions(ps, cam)
+        assert torch.allclose(first[v], alone, rtol=(2 * (n - 1) + 2) * U32, atol=0.0), v
+
+
 def test_plan_per_view_brightness_matches_rescaled_scenes():
     """A brightness sequence over the views of one plan (replayed as a CUDA graph) renders
     what separate scenes with the scaled brightness render; None restores the scales."""
