@@ -66,19 +66,44 @@ class _Pending:
         return self.first + (self.lists or 0)
 
 
+class _CudaDevice:
+    """Streams and image buffers of the server's workers on the current CUDA device."""
+
+    def __init__(self):
+        self.index = torch.cuda.current_device()
+
+    def bind(self):
+        torch.cuda.set_device(self.index)
+
+    def free_bytes(self) -> int:
+        return torch.cuda.mem_get_info()[0]
+
+    def stream(self):
+        return torch.cuda.Stream()
+
+    def image(self, height: int, width: int, stream):
+        with torch.cuda.stream(stream):
+            return torch.empty((height, width, 3), dtype=torch.float32, device="cuda")
+
+    def synchronize(self, stream):
+        stream.synchronize()
+
+
 class Server:
     """``scenes``: resident :class:`render.Scene` objects.  ``slots``: concurrent
     requests (one CUDA stream each).  ``hbm_budget``: bytes the in-flight requests may
-    reserve (default 80 % of the free device memory at construction)."""
+    reserve (default 80 % of the free device memory at construction).  ``device``: where
+    the workers' streams and images live (the current CUDA device by default; the host
+    tests of the admission logic pass a stand-in)."""
 
     def __init__(self, scenes: Sequence[render.Scene], slots: int = 4, hbm_budget: Optional[int] = None,
                  params: Optional[render.RenderParams] = None, keep_images: bool = False,
-                 max_bypass: int = 8):
+                 max_bypass: int = 8, device=None):
         self.scenes = list(scenes)
         self.slots = slots
+        self.dev = device if device is not None else _CudaDevice()
         if hbm_budget is None:
-            free, _ = torch.cuda.mem_get_info()
-            hbm_budget = int(0.8 * free)
+            hbm_budget = int(0.8 * self.dev.free_bytes())
         self.budget = int(hbm_budget)
         self.params = params or render.RenderParams()
         self.keep_images = keep_images
@@ -94,8 +119,7 @@ class Server:
         self.next_id = 0
         self.stop = False
         self.t0 = time.perf_counter()
-        self.device = torch.cuda.current_device()
-        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.streams = [self.dev.stream() for _ in range(slots)]
         self.threads = [threading.Thread(target=self._worker, args=(k,), daemon=True) for k in range(slots)]
         for t in self.threads:
             t.start()
@@ -135,7 +159,7 @@ class Server:
         self.peak_reserved = max(self.peak_reserved, self.reserved)
 
     def _worker(self, k: int):
-        torch.cuda.set_device(self.device)
+        self.dev.bind()
         stream = self.streams[k]
         while True:
             with self.cv:
@@ -148,7 +172,6 @@ class Server:
                 if p is None:
                     return
                 held = p.need  # the first part, and the lists when a count phase already ran
-                alone = self.in_flight == 0
                 self._reserve(held)
                 self.in_flight += 1
             start = self.now()
@@ -166,7 +189,10 @@ class Server:
                         held += frame.var_bytes - p.lists
                     if p.lists is None:
                         # the count phase's exact list bytes: reserve them now if they
-                        # fit, else give everything back and wait with the full footprint
+                        # fit, else give everything back and wait with the full footprint.
+                        # Past the budget only while this request is the only one in flight
+                        # (others admitted during its count phase took the free budget).
+                        alone = self.in_flight == 1
                         if self.reserved + frame.var_bytes <= self.budget or alone:
                             self._reserve(frame.var_bytes)
                             held += frame.var_bytes
@@ -174,10 +200,9 @@ class Server:
                             requeue = True
                     p.lists = frame.var_bytes
                 if not requeue:
-                    with torch.cuda.stream(stream):
-                        img = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+                    img = self.dev.image(int(cam.height), int(cam.width), stream)
                     frame.render(img, stream=stream)
-                    stream.synchronize()
+                    self.dev.synchronize(stream)
             except Exception as e:  # a failed request is reported, the server keeps going
                 with self.cv:
                     self.errors.append(f"request {p.request_id}: {e}")
@@ -185,7 +210,7 @@ class Server:
                 if frame is not None:
                     fixed, var, pairs = frame.fixed_bytes, frame.var_bytes, frame.pairs
                     frame.close()
-                    stream.synchronize()
+                    self.dev.synchronize(stream)
             finish = self.now()
             with self.cv:
                 self.reserved -= held

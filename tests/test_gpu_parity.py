@@ -158,6 +158,22 @@ def test_large_particles_cover_many_tiles():
     _compare_image("large", ps, cam, "f32", render.RenderParams(tile=16))
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_mid_size_ragged_image_with_mixed_particles(storage):
+    """A ragged 1000 x 760 image at 16-px tiles (63 x 48 tiles, the last row and column
+    partial) with small particles, particles across tile edges, a crowded spot (split
+    tiles) and large particles near the camera (binned by whole warps), against the
+    oracle."""
+    rng = np.random.default_rng(21)
+    n1, n2, n3 = 120000, 20000, 150
+    x = np.concatenate([rng.uniform(0.0, 1.0, n1), 0.5 + rng.normal(0, 0.01, n2), rng.uniform(0.3, 0.7, n3)])
+    y = np.concatenate([rng.uniform(0.0, 1.0, n1), 0.45 + rng.normal(0, 0.01, n2), rng.uniform(0.3, 0.7, n3)])
+    z = np.concatenate([rng.uniform(0.0, 1.0, n1), 0.5 + rng.normal(0, 0.01, n2), rng.uniform(1.6, 2.2, n3)])
+    h = np.concatenate([rng.uniform(0.0005, 0.006, n1), np.full(n2, 0.002), rng.uniform(0.005, 0.02, n3)])
+    ps = P.make_set(x, y, z, h, rng.uniform(0, 1, n1 + n2 + n3), beta=0.01)
+    _compare_image("mid_size", ps, synth.front_camera(1000, 760), storage, render.RenderParams(tile=16))
+
+
 def test_multi_view_render_matches_single_views():
     ps, _ = SETS["clustered"]
     cams = synth.orbit_cameras(5, 120, 90)
