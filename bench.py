@@ -382,14 +382,14 @@ def run_served(args):
 
 
 def streamed_chunks(n, chunk):
-    """Chunk sizes of splotch_render_streamed: from an eighth of `chunk` (at least 2^20),
-    doubling up to `chunk`."""
+    """Chunk sizes of splotch_render_streamed: from a sixth of `chunk` (at least 2^20),
+    growing by 3/2 up to `chunk`."""
     out, b = [], 0
-    step = max(1, min(chunk, max(chunk // 8, 1 << 20)))
+    step = max(1, min(chunk, max(chunk // 6, 1 << 20)))
     while b < n:
         out.append(min(step, n - b))
         b += out[-1]
-        step = min(chunk, 2 * step)
+        step = min(chunk, step + step // 2)
     return out
 
 

@@ -236,7 +236,7 @@ splotch_status splotch_render_ordered(splotch_scene *scene, const splotch_camera
 /* Out-of-core render of one view (Section 3.1: data sets larger than the accelerator's memory
  * go through it in double-buffered pieces, transfers overlapping work).  The particle set `desc` stays where it is (host or device, as for
  * splotch_create_scene) and is rendered in chunks of at most `chunk` particles (the first
- * an eighth of `chunk`, at least 2^20 particles, each next one twice the last, so that the
+ * a sixth of `chunk`, at least 2^20 particles, each next one 3/2 of the last, so that the
  * first transfer is short): each chunk is prepared on the device on a side stream while
  * the previous chunk renders on `stream`, and its accumulation is added to `out`.  With
  * absorption = emission the accumulation is a sum over particles, so the result equals

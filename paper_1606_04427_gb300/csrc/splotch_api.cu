@@ -1653,11 +1653,13 @@ extern "C" splotch_status splotch_render_streamed(const splotch_scene_desc *d, i
         delete sc;
     };
     const float *src[5] = {d->x, d->y, d->z, d->h, d->intensity};
-    // chunk sizes ramp up from an eighth of `chunk`, doubling: the first transfer, which
-    // nothing can hide, is short, and each later one overlaps the render of a chunk half
-    // its size (the host link moves particles faster than the frame renders them)
-    int64_t step = std::max<int64_t>(1, std::min(chunk, std::max<int64_t>(chunk / 8, (int64_t)1 << 20)));
-    for (int64_t b = 0, len = 0; b < d->n && s == SPLOTCH_OK; b += len, step = std::min(chunk, 2 * step)) {
+    // chunk sizes ramp up from a sixth of `chunk` by 3/2 per chunk: the first transfer,
+    // which nothing can hide, is short, and each later one overlaps the render of a chunk
+    // two thirds its size.  The host link moves FP32 attributes about 1.4x faster than a
+    // frame of the two-species benchmark renders them, so a faster ramp leaves the render
+    // waiting for its data, and a slower one adds chunks, each with its own kernel tails.
+    int64_t step = std::max<int64_t>(1, std::min(chunk, std::max<int64_t>(chunk / 6, (int64_t)1 << 20)));
+    for (int64_t b = 0, len = 0; b < d->n && s == SPLOTCH_OK; b += len, step = std::min(chunk, step + step / 2)) {
         len = std::min(step, d->n - b);
         splotch_scene_desc cd = *d;
         cd.n = len;
