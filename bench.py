@@ -412,7 +412,7 @@ def run_streamed(args):
         setattr(pinned, k, t.numpy())
     out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
     host_img = torch.empty_like(out, device="cpu").pin_memory()
-    chunk = args.chunk or max(4_000_000, ps.n // 4)
+    chunk = args.chunk or max(4_000_000, -(-ps.n // 3))
     for _ in range(args.warmup):
         render.render_streamed(pinned, cam, chunk, out=out, storage=storage)
     torch.cuda.synchronize()
@@ -705,7 +705,7 @@ def main():
     h2d = ps.n * 5 * 4
     d2h = cam.width * cam.height * 3 * 4
     e2e_ms = None
-    e2e_chunk = args.chunk or max(4_000_000, ps.n // 4)
+    e2e_chunk = args.chunk or max(4_000_000, -(-ps.n // 3))
     if args.e2e_steps > 0:
         pinned = ps.with_brightness(ps.brightness)
         keep = []

@@ -10,9 +10,10 @@
 //                each chunk's slice of the tile segment, and the tile's total;
 //   k_scan       turns the totals into tile segment offsets and the splat's work items;
 //   k_scatter    streams the particles again and writes a 16-byte record per
-//                (particle, tile) pair into its tile segment, in particle order (the
-//                lists come out in ascending particle index, as Section 3.2.1 builds
-//                them by walking the particles in order).
+//                (particle, tile) pair into its tile segment (each chunk's slice in the
+//                order its warps reach the records); k_scatter_stable writes every slice
+//                in ascending particle index, as Section 3.2.1 builds the lists by walking
+//                the particles in order.
 #include "splotch_internal.cuh"
 
 #include <algorithm>
