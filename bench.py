@@ -105,6 +105,11 @@ def _cached(cache_dir, key, fn):
     return ps
 
 
+# library kernels per frame (single view) and per plan launch (all views at once): count,
+# chunk-base scan, tile scan, scatter, work-item order, splat (with the final transform)
+KERNELS_PER_FRAME = 6
+
+
 def attr_bytes(storage):
     return 4 if storage == "f32" else 2
 
@@ -325,7 +330,7 @@ def run_batched(args):
                        "tile": info["tile"], "block_particles": tuned["params"].block_particles,
                        "l2": "inputs larger than L2: 0.20 GB of attributes + 0.81 GB of images per step"},
             "frames_per_s": V / (ms * 1e-3), "autotune": {"sweep_s": sweep_s, "table": tuned["table"]},
-            "plan_device_bytes": info["device_bytes"], "gpu_launches": 4 * args.steps, "clocks": clk}
+            "plan_device_bytes": info["device_bytes"], "gpu_launches": KERNELS_PER_FRAME * args.steps, "clocks": clk}
     if units:
         flops = units["pixel_pairs"] * SPLAT_FLOPS_PER_PAIR
         line["roofline"] = {"bound": "alu", "kernel": "whole batch (upper bound on the splat's time)",
@@ -789,7 +794,7 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": f"splotch_render_streamed from page-locked host memory, "
                         f"{len(streamed_chunks(n, e2e_chunk))} chunks ramping up to {e2e_chunk} particles"},
-            "gpu_launches": 4 * args.steps, "clocks": clk}
+            "gpu_launches": KERNELS_PER_FRAME * args.steps, "clocks": clk}
     if world == 1 and not args.no_extras:
         line.update(extras(ps, cam, params, args, local))
     if not args.no_cpu_baseline:

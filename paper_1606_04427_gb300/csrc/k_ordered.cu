@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(kOWarps * 32, 4)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total_items) break;
 
-        const int slice = item / S2, q = item - slice * S2;
+        const int qs = item / S2, q = item - qs * S2;
+        const int slice = fr.order ? __ldg(&fr.order[qs]) : qs;  // largest slices first
         const int gt = find_tile_o(fr.item_off, N, slice);
         const int v = gt / nt, t = gt - v * nt;
         const int chunk = slice - fr.item_off[gt];
@@ -415,6 +416,7 @@ cudaError_t launch_splat_ordered(const SceneDev &sc, const FrameDev &fr, int *qu
                                  const float *absorb, float *ord_scratch, int map_out, int grid, cudaStream_t st) {
     cudaError_t err = ensure_smem_limit((const void *)k_splat_ordered, ordered_smem());
     if (err != cudaSuccess) return err;
+    if ((err = launch_item_order(fr, st)) != cudaSuccess) return err;
     k_splat_ordered<<<grid, kOWarps * 32, ordered_smem(), st>>>(sc, fr, queue, out, ordered_split(fr.T), absorb,
                                                                 ord_scratch, map_out);
     return cudaGetLastError();

@@ -101,8 +101,9 @@ __global__ void __launch_bounds__(kSplatThreads, 3) k_splat(SceneDev sc, FrameDe
     for (;;) {
         if (tid == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();
-        const int item = s_item;
-        if (item >= total_items) break;
+        const int qi = s_item;
+        if (qi >= total_items) break;
+        const int item = fr.order ? __ldg(&fr.order[qi]) : qi;
 
         const int gt = find_tile(fr.item_off, N, item);
         const int v = gt / nt, t = gt - v * nt;
@@ -482,7 +483,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (WarpShape<NR, NC>::kMinCta
 
         // item = (slice of a tile list, square of the tile); the squares of a slice are
         // consecutive items, so they run at once and share the slice's records in L2
-        const int slice = item / S2, q = item - slice * S2;
+        const int qs = item / S2, q = item - qs * S2;
+        const int slice = fr.order ? __ldg(&fr.order[qs]) : qs;
         const int gt = find_tile(fr.item_off, N, slice);
         const int v = gt / nt, t = gt - v * nt;
         const int chunk = slice - fr.item_off[gt];
@@ -745,8 +747,64 @@ int splat_blocks_per_sm(int T) {
 
 int splat_workers_per_sm(int T) { return splat_blocks_per_sm(T) * (warp_kernel(T) ? kWarpsPerCta : 1); }
 
+// k_item_order: one CTA.  The splat's work items (tile-list slices) ordered by record count,
+// largest first, so that the items taken last by the workers are the short ones and the
+// kernel does not end waiting for a few long slices started late.  Slices fall into
+// kOrderBins bins of equal width up to K (the slice length of a split tile); within a bin
+// the order is that of the atomic cursors.  Each item writes its own tile, or adds into
+// the exact accumulators of a split tile, so images do not depend on the order.
+constexpr int kOrderBins = 64;
+
+__global__ void __launch_bounds__(1024) k_item_order(FrameDev fr) {
+    __shared__ int s_cnt[kOrderBins];
+    if (fr.status[kStatOverflow]) return;
+    const int N = fr.V * fr.n_tiles;
+    const long long K = fr.sizes[kSizeK];
+    auto bin_of = [&](long long size) -> int {
+        return (int)min((long long)(kOrderBins - 1), size * kOrderBins / (K + 1));
+    };
+    for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    // (1) slices per size bin: every slice of a split tile holds K records but the last
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        const int i0 = fr.item_off[t], n = fr.item_off[t + 1] - i0;
+        const long long c = fr.counts[t];
+        if (n > 1) atomicAdd(&s_cnt[bin_of(K)], n - 1);
+        atomicAdd(&s_cnt[bin_of(c - K * (n - 1))], 1);
+    }
+    __syncthreads();
+    // (2) bin starts, the largest bin first
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = kOrderBins - 1; b >= 0; --b) {
+            const int c = s_cnt[b];
+            s_cnt[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // (3) every slice at its bin's next place
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        const int i0 = fr.item_off[t], n = fr.item_off[t + 1] - i0;
+        const long long c = fr.counts[t];
+        if (n > 1) {
+            const int p = atomicAdd(&s_cnt[bin_of(K)], n - 1);
+            for (int s = 0; s < n - 1; ++s) fr.order[p + s] = i0 + s;
+        }
+        fr.order[atomicAdd(&s_cnt[bin_of(c - K * (n - 1))], 1)] = i0 + n - 1;
+    }
+}
+
+cudaError_t launch_item_order(const FrameDev &fr, cudaStream_t st) {
+    if (!fr.order) return cudaSuccess;
+    k_item_order<<<1, 1024, 0, st>>>(fr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_splat(const SceneDev &sc, const FrameDev &fr, int *queue, float *out, int out_accum,
                          int grid, cudaStream_t st) {
+    cudaError_t e = launch_item_order(fr, st);
+    if (e != cudaSuccess) return e;
     const size_t smem = splat_smem(fr.T);
     const bool scaled = fr.vscale != nullptr, emit = sc.emit != nullptr;
     cudaError_t err = ensure_smem_limit(

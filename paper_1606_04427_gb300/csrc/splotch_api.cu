@@ -670,7 +670,8 @@ struct FrameHost {
     int64_t pair_cap = 0;
     int item_cap = 0, split_cap = 0;
     bool pids = false;
-    size_t o_lists, o_pids, o_scratch, o_tickets, var_bytes;
+    bool order = false;  // the splat takes its work items largest first (k_item_order)
+    size_t o_lists, o_pids, o_scratch, o_tickets, o_order = 0, var_bytes;
 };
 
 static const int64_t kRelBudget = 256ll << 20;
@@ -714,16 +715,20 @@ static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_ti
 // Exact accumulators of one split tile: 3 channels x T x T pixels, 16 bytes each.
 static size_t split_scratch_bytes(int T) { return sizeof(unsigned long long) * 2 * 3 * (size_t)T * T; }
 
-static void layout_var(FrameHost &fh, int64_t pairs, int items, int splits, bool pids) {
+// order: room for the splat's item order (one int per work item; the fixed-array render
+// takes its items in tile order).
+static void layout_var(FrameHost &fh, int64_t pairs, int items, int splits, bool pids, bool order = true) {
     fh.pair_cap = pairs;
     fh.item_cap = items;
     fh.split_cap = splits;
     fh.pids = pids;
+    fh.order = order;
     Carve cv;
     fh.o_lists = cv.take(sizeof(float4) * std::max<int64_t>(1, pairs));
     fh.o_pids = pids ? cv.take(sizeof(int) * std::max<int64_t>(1, pairs)) : 0;
     fh.o_scratch = cv.take(split_scratch_bytes(fh.T) * std::max(1, splits));
     fh.o_tickets = cv.take(sizeof(int) * std::max(1, splits));
+    fh.o_order = order ? cv.take(sizeof(int) * (size_t)std::max(1, items)) : 0;
     fh.var_bytes = cv.off;
 }
 
@@ -748,6 +753,7 @@ static FrameDev frame_dev(const FrameHost &fh, char *fixed, char *var) {
         fr.pids = fh.pids ? (int *)(var + fh.o_pids) : nullptr;
         fr.scratch = (unsigned long long *)(var + fh.o_scratch);
         fr.tickets = (int *)(var + fh.o_tickets);
+        fr.order = fh.order ? (int *)(var + fh.o_order) : nullptr;
     }
     fr.pair_cap = var ? fh.pair_cap : INT64_MAX;
     fr.item_cap = var ? fh.item_cap : INT32_MAX;
@@ -1503,7 +1509,7 @@ extern "C" splotch_status splotch_render_noalloc(splotch_scene *sc, const splotc
         return fail(SPLOTCH_ERR_UNSUPPORTED, "%d tiles of %d px need %zu bytes of tables, more than the %zu-byte fixed workspace",
                     vp.n_tiles, T, fixed + scratch, kStaticBytes);
     const int64_t pairs = (int64_t)((kStaticBytes - fixed - scratch - 1024) / sizeof(float4));
-    layout_var(fh, pairs, INT32_MAX, splits, false);
+    layout_var(fh, pairs, INT32_MAX, splits, false, false);
     if (fixed + fh.var_bytes > kStaticBytes)
         return fail(SPLOTCH_ERR_UNSUPPORTED, "fixed workspace layout overflow");
     char *var = base + fixed;

@@ -79,6 +79,8 @@ struct FrameDev {
     int *pids;                // [pair capacity] particle index per record, or null
     unsigned long long *scratch;  // [split capacity][3][T][T][2] exact accumulators (fix_add)
     int *tickets;                 // [split capacity]
+    int *order;                   // [item capacity] work items, largest first (k_item_order), or
+                                  // null: items in tile order
     int64_t pair_cap;
     int item_cap, split_cap;
     const float *vscale;      // [V * n_types] emission scale per view and species, or null
@@ -404,6 +406,9 @@ cudaError_t launch_gather_records(const float4 *src, const uint32_t *idx, int64_
 int ordered_split(int T);
 int ordered_ctas_per_sm();
 int ordered_workers_per_sm();
+// Work items of the frame ordered largest first into fr.order (k_item_order; no-op when
+// fr.order is null).
+cudaError_t launch_item_order(const FrameDev &fr, cudaStream_t st);
 cudaError_t launch_splat_ordered(const SceneDev &sc, const FrameDev &fr, int *queue, float *out,
                                  const float *absorb, float *ord_scratch, int map_out, int grid, cudaStream_t st);
 size_t splat_smem_bytes(int T);
