@@ -675,6 +675,7 @@ struct FrameHost {
 };
 
 static const int64_t kRelBudget = 256ll << 20;
+static const int kChunkPerEntry = 8;  // particles per histogram entry in a binning chunk
 
 static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_tiles, int T,
                          int block_particles = 0, int64_t rel_budget = kRelBudget) {
@@ -688,9 +689,20 @@ static void layout_fixed(FrameHost &fh, const splotch_scene *sc, int V, int n_ti
     const int64_t unit = (int64_t)kThreads * vec;
     const int64_t n_units = std::max<int64_t>(1, (sc->n + unit - 1) / unit);
     const int groups = (V + fh.G - 1) / fh.G;
-    // two whole waves of the binning kernels over all view groups
+    // Chunks of the binning kernels: whole waves over all view groups, as many as four where
+    // every chunk keeps at least kChunkPerEntry particles per histogram entry (its fixed cost
+    // is clearing and writing one count per tile), never fewer than two.  With two waves the
+    // chunks' unequal costs (a gas particle makes about twice the records of a star) left the
+    // last wave's SMs idle for about a sixth of the scatter; a chunk count just above a whole
+    // number of waves would add a wave for a few CTAs.
     const int occ = bin_ctas_per_sm(sc->storage, sizeof(int) * (size_t)fh.G * n_tiles);
+    const int64_t min_chunk = (int64_t)kChunkPerEntry * fh.G * n_tiles;
+    const int64_t max_by_size = std::max<int64_t>(1, sc->n / std::max<int64_t>(1, min_chunk));
     int64_t target = std::max<int64_t>(1, (2ll * n_sm * occ + groups - 1) / groups);
+    for (int64_t w = 3; w <= 4; ++w) {
+        const int64_t t = std::max<int64_t>(1, (w * n_sm * occ + groups - 1) / groups);
+        if (t <= max_by_size) target = t;
+    }
     target = std::min(target, n_units);
     const int64_t max_chunks = std::max<int64_t>(1, rel_budget / (4ll * V * n_tiles));
     int64_t nch = std::min(target, max_chunks);
